@@ -1,0 +1,103 @@
+/*
+ * rotseq.h -- C ABI of the GB300 (sm_103a) library that applies a sequence of
+ * planar (Givens) rotations to the columns of a dense matrix.
+ *
+ * Method: Steel & Langou, "Communication efficient application of sequences
+ * of planar rotations to a matrix".
+ *
+ * Problem (Algorithm 2, rot_sequence): A is m x n, C and S are (n-1) x k.
+ * For p = 0..k-1 and j = 0..n-2, in that order, rotation (j,p) replaces
+ * columns j and j+1 of A by (Algorithm 1, rot)
+ *     A(:,j)   <-  c*A(:,j) + s*A(:,j+1)
+ *     A(:,j+1) <- -s*A(:,j) + c*A(:,j+1)        with c = C(j,p), s = S(j,p),
+ * i.e. A <- A * G(0,0) G(1,0) ... G(n-2,k-1) applied from the right.
+ *
+ * Layout: every matrix is column-major with a leading dimension:
+ *     A(i,j) = A[i + j*lda],  C(j,p) = C[j + p*ldc],  S(j,p) = S[j + p*lds].
+ * Pointers named A, C, S are DEVICE pointers unless the name says host.
+ *
+ * Ownership: the caller owns A, C and S.  A is updated in place.  C and S
+ * must stay unmodified until the work queued on `stream` has finished.  The
+ * library owns only its scratch memory, which it takes from the CUDA
+ * stream-ordered allocator of the current device and returns on the same
+ * stream.
+ *
+ * Execution: every rot_apply* call is asynchronous on `stream` (a
+ * cudaStream_t passed as void*, NULL = legacy default stream) and uses the
+ * current CUDA device.  A call returns once the work is queued.  Device-side
+ * failures (a bounded wait that ran out) are recorded in a sticky status that
+ * rot_device_status() returns.
+ *
+ * Errors: no entry point aborts or exits.  Quick return (ROT_OK, nothing
+ * queued) when m == 0, n <= 1 or k == 0.
+ *   ROT_EINVAL   a size < 0, lda < max(1,m), ldc or lds < max(1,n-1), a NULL
+ *                pointer with work to do, or a size beyond the limits below.
+ *   ROT_ENOMEM   scratch memory could not be obtained.
+ *   ROT_ECUDA    a CUDA call or launch failed.
+ * Limits: m, n, k and n+k must each be below 2^31.
+ *
+ * FMA placement: the FP64 and FP32 paths compute every rotation as
+ *     x' = fma(c, x, RN(s*y)),   y' = fma(c, y, -RN(s*x)),
+ * which makes the FP64 result bit-identical to a plain loop over Algorithm 2
+ * with the same placement.
+ */
+#ifndef ROTSEQ_H
+#define ROTSEQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ROT_OK = 0,
+  ROT_EINVAL = 1,
+  ROT_ECUDA = 2,
+  ROT_ENOMEM = 3,
+  ROT_ETIMEOUT = 4,
+  ROT_EBUSY = 5,
+  ROT_EUNSUPPORTED = 6
+} rot_status;
+
+/* Library version: major*10000 + minor*100 + patch. */
+int rot_version(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* rot_status_string(rot_status s);
+
+/*
+ * Algorithm 2 in FP64, computed in the wave order of Algorithm 3
+ * (Section 1.1) by the row-parallel wavefront kernel.  Bit-identical to the
+ * plain loop of Algorithm 2 with the FMA placement above.
+ *   m, n, k   sizes (A is m x n; C, S are (n-1) x k)
+ *   A, lda    device FP64, column-major, updated in place
+ *   C, ldc    device FP64 cosines, column-major
+ *   S, lds    device FP64 sines, column-major
+ *   stream    cudaStream_t (as void*) the work is queued on
+ */
+rot_status rot_apply(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
+                     int64_t ldc, const double* S, int64_t lds, void* stream);
+
+/*
+ * Algorithm 2 in FP32 (FP32 data, FP32 rotations, FP32 fused multiply-add),
+ * same kernel design and argument meaning as rot_apply.  Bit-identical to a
+ * plain FP32 loop of Algorithm 2 with the FMA placement above; against the
+ * FP64 result the per-row relative error stays below 8*k*2^-24.
+ */
+rot_status rot_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C,
+                         int64_t ldc, const float* S, int64_t lds, void* stream);
+
+/*
+ * Synchronizes the current device, then returns and clears the sticky
+ * device status: ROT_OK, or ROT_ETIMEOUT if a kernel's bounded wait ran out
+ * since the last call, or ROT_ECUDA if the device reported an error.
+ */
+rot_status rot_device_status(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROTSEQ_H */

@@ -1,0 +1,83 @@
+"""ctypes view of the C ABI in include/rotseq.h (argument marshalling only).
+
+The shared library must have been built (``paper_2412_01852_gb300.build.build()``
+or ``__graft_entry__.build()``).  There is no fallback: if the library is
+missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+i64 = ctypes.c_int64
+vp = ctypes.c_void_p
+ci = ctypes.c_int
+sz = ctypes.c_size_t
+
+# name -> (restype, argtypes); must match include/rotseq.h
+SIGNATURES = {
+    "rot_version": (ci, []),
+    "rot_status_string": (ctypes.c_char_p, [ci]),
+    "rot_apply": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "rot_apply_f32": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "rot_device_status": (ci, []),
+}
+
+
+class RotError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = int(code)
+        super().__init__("%s%s" % (where + ": " if where else "", status_string(code)))
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    "the CUDA library %s is not built; run paper_2412_01852_gb300.build.build() "
+                    "(there is no CPU fallback)" % path)
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def status_string(code) -> str:
+    try:
+        return load().rot_status_string(int(code)).decode()
+    except Exception:
+        return "rot_status %d" % int(code)
+
+
+def check(code, where=""):
+    if int(code) != 0:
+        raise RotError(code, where)
+
+
+def header_functions(path=None):
+    """Names of the functions declared in include/rotseq.h (used by the ABI test)."""
+    if path is None:
+        path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "rotseq.h")
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b([a-z_][a-z0-9_]*)\s*\([^;{]*\)\s*;", text)
+    return sorted(set(n for n in names if n.startswith("rot_")))

@@ -1,0 +1,84 @@
+"""Python binding of the C ABI with the same names, taking torch CUDA tensors.
+
+Only marshalling happens here: shapes, leading dimensions, raw device
+pointers and the current CUDA stream are passed to the library; every step of
+the computation runs in its kernels.  Matrices are column-major: a tensor of
+shape (rows, cols) with stride(0) == 1; ``colmajor`` and ``empty_colmajor``
+make such tensors.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _native
+
+
+def empty_colmajor(rows, cols, dtype=torch.float64, device="cuda"):
+    """Uninitialised column-major (rows x cols) tensor (leading dimension = rows)."""
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def colmajor(t: torch.Tensor) -> torch.Tensor:
+    """Column-major copy of a 2-D tensor (same values)."""
+    out = empty_colmajor(t.shape[0], t.shape[1], dtype=t.dtype, device=t.device)
+    out.copy_(t)
+    return out
+
+
+def _ld(t: torch.Tensor, rows: int) -> int:
+    if t.dim() != 2:
+        raise ValueError("expected a 2-D tensor")
+    if t.shape[0] > 1 and t.shape[1] > 1 and t.stride(0) != 1:
+        raise ValueError("expected a column-major tensor (stride(0) == 1)")
+    if t.shape[1] > 1:
+        return max(int(t.stride(1)), max(1, rows))
+    return max(1, rows)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes_void(stream.cuda_stream)
+
+
+def ctypes_void(h):
+    return int(h) if h else None
+
+
+def _ptr(t):
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def _args(A, C, S, dtype):
+    for name, t in (("A", A), ("C", C), ("S", S)):
+        if t.dtype != dtype:
+            raise TypeError("%s must be %s" % (name, dtype))
+        if t.numel() > 0 and not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+    m, n = A.shape
+    nm1 = max(n - 1, 0)
+    if C.shape != S.shape or (n >= 2 and C.shape[0] != nm1):
+        raise ValueError("C and S must both be (n-1) x k")
+    k = C.shape[1] if n >= 2 else (C.shape[1] if C.dim() == 2 else 0)
+    return (m, n, k, _ptr(A), _ld(A, m), _ptr(C), _ld(C, nm1), _ptr(S), _ld(S, nm1))
+
+
+def rot_apply(A, C, S, stream=None):
+    """Algorithm 2 in FP64 on device tensors, in place on A (column-major)."""
+    lib = _native.load()
+    _native.check(lib.rot_apply(*_args(A, C, S, torch.float64), _stream_handle(stream)), "rot_apply")
+    return A
+
+
+def rot_apply_f32(A, C, S, stream=None):
+    """Algorithm 2 in FP32 on device tensors, in place on A (column-major)."""
+    lib = _native.load()
+    _native.check(lib.rot_apply_f32(*_args(A, C, S, torch.float32), _stream_handle(stream)),
+                  "rot_apply_f32")
+    return A
+
+
+def rot_device_status():
+    """Synchronize; raise RotError if a kernel recorded a device-side failure."""
+    lib = _native.load()
+    _native.check(lib.rot_device_status(), "rot_device_status")

@@ -1,0 +1,71 @@
+// rs_api.cu -- the extern "C" entry points declared in include/rotseq.h:
+// argument validation, quick returns, dispatch to the kernels.
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "rs_internal.h"
+
+namespace {
+
+constexpr int64_t kLimit = (int64_t(1) << 31) - 1;
+
+rot_status validate(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* C,
+                    int64_t ldc, const void* S, int64_t lds, bool* quick) {
+  *quick = false;
+  if (m < 0 || n < 0 || k < 0) return ROT_EINVAL;
+  if (m > kLimit || n > kLimit || k > kLimit || n + k > kLimit) return ROT_EINVAL;
+  if (lda < (m > 1 ? m : 1)) return ROT_EINVAL;
+  const int64_t nm1 = n - 1 > 1 ? n - 1 : 1;
+  if (ldc < nm1 || lds < nm1) return ROT_EINVAL;
+  if (m == 0 || n <= 1 || k == 0) {
+    *quick = true;
+    return ROT_OK;
+  }
+  if (!A || !C || !S) return ROT_EINVAL;
+  return ROT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rot_version(void) { return 100; }
+
+const char* rot_status_string(rot_status s) {
+  switch (s) {
+    case ROT_OK: return "ROT_OK";
+    case ROT_EINVAL: return "ROT_EINVAL: invalid argument";
+    case ROT_ECUDA: return "ROT_ECUDA: CUDA error";
+    case ROT_ENOMEM: return "ROT_ENOMEM: out of device memory";
+    case ROT_ETIMEOUT: return "ROT_ETIMEOUT: a bounded wait ran out";
+    case ROT_EBUSY: return "ROT_EBUSY: resource busy";
+    case ROT_EUNSUPPORTED: return "ROT_EUNSUPPORTED: not supported on this device";
+  }
+  return "ROT_?: unknown status";
+}
+
+rot_status rot_apply(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
+                     int64_t ldc, const double* S, int64_t lds, void* stream) {
+  bool quick;
+  rot_status v = validate(m, n, k, A, lda, C, ldc, S, lds, &quick);
+  if (v != ROT_OK || quick) return v;
+  return rs::wave_apply<double>(m, n, k, A, lda, C, ldc, S, lds,
+                                static_cast<cudaStream_t>(stream), rs::WaveOptions{});
+}
+
+rot_status rot_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C,
+                         int64_t ldc, const float* S, int64_t lds, void* stream) {
+  bool quick;
+  rot_status v = validate(m, n, k, A, lda, C, ldc, S, lds, &quick);
+  if (v != ROT_OK || quick) return v;
+  return rs::wave_apply<float>(m, n, k, A, lda, C, ldc, S, lds,
+                               static_cast<cudaStream_t>(stream), rs::WaveOptions{});
+}
+
+rot_status rot_device_status(void) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return ROT_ECUDA;
+  const int s = rs::take_sticky_status();
+  if (s < 0) return ROT_ECUDA;
+  return s == 0 ? ROT_OK : ROT_ETIMEOUT;
+}
+
+}  // extern "C"

@@ -1,0 +1,37 @@
+// rs_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include "../../include/rotseq.h"
+
+namespace rs {
+
+// Per-call overrides of the wavefront kernel's tiling (0 = planner default).
+struct WaveOptions {
+  int K = 0;            // sequences per p-block (<= the kernel's window KMAX)
+  int NB = 0;           // waves per work item
+  int ctas_per_sm = 0;  // resident CTAs per SM (<= occupancy limit)
+};
+
+struct WavePlan {
+  int K, NB, delta, nchains, G, B, kpad, cs_rows;
+  long long total;
+};
+
+WavePlan plan_wave(int64_t m, int64_t n, int64_t k, int kmax, int nbt, int K_req, int NB_req,
+                   int elem_bytes);
+
+template <typename T>
+rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
+                      const T* S, int64_t lds, cudaStream_t stream, const WaveOptions& opt);
+
+bool encode_tile_map_2d(CUtensorMap* map, const void* base, bool is_double, uint64_t inner,
+                        uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
+                        uint32_t box_outer);
+
+// Sticky device status (first error recorded by any launch since the last read).
+int take_sticky_status();
+void record_status_async(const int* status, cudaStream_t stream);
+
+}  // namespace rs

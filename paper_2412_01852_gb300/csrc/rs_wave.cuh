@@ -1,0 +1,273 @@
+// rs_wave.cuh -- the row-parallel wavefront kernel that applies a sequence of
+// planar rotations to the columns of a column-major matrix (Algorithm 2's
+// result, computed in Algorithm 3's wave order, Section 1.1).
+//
+// Work decomposition (GB300 design; the paper's blocking of Section 2 recast
+// for warps):
+//   chain c      : 32 consecutive rows of one instance, one row per lane.
+//   p-block g    : sequences [g*K, g*K + kr), kr = min(K, k - g*K).
+//   wave-block b : waves [b*NB, (b+1)*NB) of that p-block; wave w holds the
+//                  rotations (j = w - l, p = g*K + l), l = 0..kr-1, in
+//                  increasing l (Section 1.1: (i,j), (i-1,j+1), ...).
+// An item (c, g, b) is one warp's unit of work.  Item (c,g,b) needs item
+// (c,g,b-1) (the same rows' earlier waves of the same sequences) and enough
+// of p-block g-1 to have finished every column it touches (the dependency
+// rule of Section 2: block (j_b, p_b) before (j_b + n_b, p_b) and before
+// (j_b - k_b, p_b + k_b)).  Items are handed out in increasing key
+// b + delta*g by an atomic ticket, so every dependency holds a smaller ticket
+// and is held by a running warp: no co-residency is needed and no deadlock
+// can occur.  Between items the partially rotated columns live in A itself.
+//
+// Inside an item a warp keeps a window of KMAX+1 columns in registers.  Each
+// wave loads one new column (coalesced: 32 lanes x one element), applies kr
+// rotations to the window and retires the oldest column.  (c, s) pairs for the
+// item's waves come from a wave-major repacked copy of C and S, staged into
+// shared memory per warp by TMA (cp.async.bulk.tensor, double-buffered,
+// completion on an mbarrier), and are read back with broadcast loads.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include "rs_device.cuh"
+
+namespace rs {
+
+template <typename T> struct Pair;
+template <> struct Pair<double> { using type = double2; };
+template <> struct Pair<float> { using type = float2; };
+
+// Algorithm 1 with the fixed FMA placement:
+//   x' = fma(c, x, RN(s*y)),  y' = fma(c, y, -RN(s*x)).
+__device__ __forceinline__ void rotate(double& x, double& y, double c, double s) {
+  const double sy = __dmul_rn(s, y);
+  const double sx = __dmul_rn(s, x);
+  const double xn = __fma_rn(c, x, sy);
+  y = __fma_rn(c, y, -sx);
+  x = xn;
+}
+__device__ __forceinline__ void rotate(float& x, float& y, float c, float s) {
+  const float sy = __fmul_rn(s, y);
+  const float sx = __fmul_rn(s, x);
+  const float xn = __fmaf_rn(c, x, sy);
+  y = __fmaf_rn(c, y, -sx);
+  x = xn;
+}
+
+// One instance of the problem as the wave kernel sees it.
+struct WaveProblem {
+  void* A;          // column-major m x n, leading dimension lda (elements)
+  int64_t lda;
+  int m, n, k;
+  int K;            // sequences per p-block
+  int NB;           // waves per item
+  int delta;        // key stride between p-blocks: 1 + ceil(K / NB)
+  int nchains;      // ceil(m / 32)
+  int G;            // p-blocks: ceil(k / K)
+  int B;            // wave-blocks of a full p-block: ceil((n + K - 2) / NB)
+  int cs_row0;      // first row of this instance in the repacked (c,s) tensor
+  int* done;        // [nchains * G] completed wave-blocks per (chain, p-block)
+  unsigned long long* ticket;  // next ticket to hand out
+  int* status;      // first device error of this launch (0 = none)
+  long long total;  // nchains * G * B items
+};
+
+// Number of (g, b) pairs whose key b + delta*g equals kappa.
+__device__ __forceinline__ int pairs_in_key(int kappa, int G, int B, int delta, int* g_lo) {
+  int hi = kappa / delta;
+  if (hi > G - 1) hi = G - 1;
+  int lo = kappa - (B - 1);
+  lo = lo <= 0 ? 0 : (lo + delta - 1) / delta;
+  *g_lo = lo;
+  return hi >= lo ? hi - lo + 1 : 0;
+}
+
+// Repack C, S ((n-1) x k, column-major) into rows of (c, s) pairs indexed by
+// j + p: out[(row0 + j + p) * W2 + 2p + {0,1}] = (C(j,p), S(j,p)).  Item
+// (c,g,b) then finds all pairs of its wave w in row w + g*K, columns
+// [2gK, 2gK + 2kr): a rectangle that TMA can fetch.
+template <typename T>
+__global__ void repack_cs_kernel(const T* __restrict__ C, int64_t ldc, const T* __restrict__ S,
+                                 int64_t lds, int n, int k, T* __restrict__ out, int64_t W2,
+                                 int row0) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y * blockDim.y + threadIdx.y;
+  if (j >= n - 1 || p >= k) return;
+  typename Pair<T>::type v;
+  v.x = C[j + (int64_t)p * ldc];
+  v.y = S[j + (int64_t)p * lds];
+  *reinterpret_cast<typename Pair<T>::type*>(out + (int64_t)(row0 + j + p) * W2 + 2 * p) = v;
+}
+
+template <typename T, int KMAX, int NBT>
+struct WaveSmem {
+  static constexpr int kTileElems = NBT * 2 * KMAX;              // one buffer
+  static constexpr int kTileBytes = kTileElems * (int)sizeof(T);
+  static constexpr int kWarpBytes = 2 * kTileBytes + 128;         // 2 buffers + barriers
+};
+
+// The kernel.  Every warp runs the ticket loop independently; warps of a CTA
+// share nothing but the CTA's shared-memory allocation.
+template <typename T, int KMAX, int NBT, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+wave_kernel(const __grid_constant__ CUtensorMap tmap, const WaveProblem P) {
+  using V2 = typename Pair<T>::type;
+  using SM = WaveSmem<T, KMAX, NBT>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  unsigned char* wbase = smem_raw + warp * SM::kWarpBytes;
+  auto tile = [&](int i) { return reinterpret_cast<T*>(wbase + i * SM::kTileBytes); };
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + 2 * SM::kTileBytes);
+
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbarrier_init();
+    prefetch_tmap(&tmap);
+  }
+  __syncwarp();
+  uint32_t phase0 = 0, phase1 = 0;
+
+  // Ticket -> key cursor (tickets a warp receives only increase).
+  int kappa = 0;
+  long long kstart = 0;
+  int kglo = 0;
+  int kcount = pairs_in_key(0, P.G, P.B, P.delta, &kglo) * P.nchains;
+
+  T* const A = reinterpret_cast<T*>(P.A);
+  const int n = P.n;
+
+  while (true) {
+    long long t = 0;
+    if (lane == 0) t = (long long)atomicAdd(P.ticket, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= P.total) break;
+    if (lane == 0 && ld_relaxed_gpu(P.status) != 0) t = -1;
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t < 0) break;
+
+    const int last_key = (P.B - 1) + P.delta * (P.G - 1);
+    while (t >= kstart + kcount && kappa <= last_key) {
+      kstart += kcount;
+      ++kappa;
+      kcount = pairs_in_key(kappa, P.G, P.B, P.delta, &kglo) * P.nchains;
+    }
+    if (kappa > last_key) {                    // cannot happen: keys cover every ticket
+      if (lane == 0) set_error(P.status, kDevBadItem);
+      break;
+    }
+    const long long r = t - kstart;
+    const int gi = (int)(r / P.nchains);
+    const int c = (int)(r - (long long)gi * P.nchains);
+    const int g = kglo + gi;
+    const int b = kappa - P.delta * g;
+    const int p0 = g * P.K;
+    const int kr = min(P.K, P.k - p0);
+    const int nw = n + kr - 2;                 // waves of this p-block
+    const int w0 = b * P.NB;
+    if (w0 >= nw) continue;                    // empty tail item of a short p-block
+    const int w1 = min(w0 + P.NB, nw);
+    int* const done = P.done + (int64_t)c * P.G;
+
+    // ---- wait for dependencies ------------------------------------------------
+    bool ok = true;
+    if (lane == 0) {
+      if (b > 0) ok = wait_flag_geq(done + g, b, P.status);
+      if (ok && g > 0) {
+        const int krp = P.K;                   // every p-block but the last is full
+        const int nwp = n + krp - 2;
+        const int Bp = (nwp + P.NB - 1) / P.NB;
+        int need = (w1 + krp + P.NB - 1) / P.NB;
+        if (need > Bp) need = Bp;
+        ok = wait_flag_geq(done + g - 1, need, P.status);
+      }
+      if (!ok) set_error(P.status, kDevTimeoutDependency);
+    }
+    ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
+    if (!ok) break;
+
+    // ---- load the window: columns [w0-kr+1, w0] owned by this p-block ---------
+    const int row = c * 32 + lane;
+    const bool rowok = row < P.m;
+    T* const arow = A + row;
+    const int own_lo = w0 - kr + 1;
+    T win[KMAX + 1];
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) {
+      const int q = w0 + 1 - KMAX + s;
+      win[s] = (rowok && q >= own_lo && q >= 0 && q <= n - 1) ? ld_cg(arow + (int64_t)q * P.lda) : T(0);
+    }
+    T nextcol = (rowok && w0 + 1 <= n - 1) ? ld_cg(arow + (int64_t)(w0 + 1) * P.lda) : T(0);
+
+    // ---- stream (c,s) tiles and run the waves ---------------------------------
+    const int ntiles = (w1 - w0 + NBT - 1) / NBT;
+    const int tx = 2 * p0;
+    const int ty0 = P.cs_row0 + w0 + p0;
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[0], SM::kTileBytes);
+      tma_load_2d(tile(0), &tmap, &bar[0], tx, ty0);
+    }
+    for (int st = 0; st < ntiles; ++st) {
+      const int cur = st & 1;
+      if (st + 1 < ntiles && lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[cur ^ 1], SM::kTileBytes);
+        tma_load_2d(tile(cur ^ 1), &tmap, &bar[cur ^ 1], tx, ty0 + (st + 1) * NBT);
+      }
+      const uint32_t ph = cur ? phase1 : phase0;
+      if (!mbar_wait_bounded(&bar[cur], ph)) {
+        if (lane == 0) set_error(P.status, kDevTimeoutTma);
+        ok = false;
+      }
+      if (cur) phase1 ^= 1u; else phase0 ^= 1u;
+      if (!__all_sync(0xffffffffu, ok)) {
+        // Let the copy already issued into the other buffer land before leaving.
+        if (st + 1 < ntiles) (void)mbar_wait_bounded(&bar[cur ^ 1], cur ? phase0 : phase1);
+        ok = false;
+        break;
+      }
+      const V2* tl = reinterpret_cast<const V2*>(tile(cur));
+      const int ws = w0 + st * NBT;
+      const int wend = min(ws + NBT, w1);
+      for (int w = ws; w < wend; ++w) {
+        win[KMAX] = nextcol;
+        nextcol = (rowok && w + 2 <= n - 1) ? ld_cg(arow + (int64_t)(w + 2) * P.lda) : T(0);
+        const int l_lo = max(0, w - (n - 2));
+        const int l_hi = min(kr - 1, w);
+        const V2* trow = tl + (w - ws) * KMAX;
+        // Rotations l = l_lo..l_hi in increasing l.  The bounds are the same
+        // for all lanes, so the early exit is a uniform branch and a short
+        // p-block issues only its own kr rotations.
+#pragma unroll
+        for (int l = 0; l < KMAX; ++l) {
+          if (l > l_hi) break;
+          if (l >= l_lo) {
+            const V2 cs = trow[l];
+            rotate(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
+          }
+        }
+        const int q = w + 1 - KMAX;            // column leaving the window
+        if (rowok && q >= own_lo && q >= 0) st_cg(arow + (int64_t)q * P.lda, win[0]);
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) win[s] = win[s + 1];
+      }
+      __syncwarp();
+    }
+    if (!ok) break;
+
+    // ---- flush the window: columns [w1+1-KMAX, w1] ----------------------------
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) {
+      const int q = w1 + 1 - KMAX + s;
+      if (rowok && q >= own_lo && q >= 0 && q <= n - 1) st_cg(arow + (int64_t)q * P.lda, win[s]);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      st_release_gpu(done + g, b + 1);
+    }
+  }
+}
+
+}  // namespace rs

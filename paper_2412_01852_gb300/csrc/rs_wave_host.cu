@@ -1,0 +1,182 @@
+// rs_wave_host.cu -- host side of the wavefront kernel: planning, scratch
+// memory, the repack of C/S, the TMA tensor map and the launch.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "rs_wave.cuh"
+#include "rs_internal.h"
+
+namespace rs {
+
+// Sticky device status: the first error any launch of this library recorded.
+__device__ int g_sticky_status = 0;
+
+__global__ void accumulate_status_kernel(const int* status) {
+  const int s = *status;
+  if (s != 0) atomicCAS(&g_sticky_status, 0, s);
+}
+
+int take_sticky_status() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_sticky_status, sizeof(int)) != cudaSuccess) return -1;
+  const int zero = 0;
+  if (cudaMemcpyToSymbol(g_sticky_status, &zero, sizeof(int)) != cudaSuccess) return -1;
+  return v;
+}
+
+void record_status_async(const int* status, cudaStream_t stream) {
+  accumulate_status_kernel<<<1, 1, 0, stream>>>(status);
+}
+
+// ---- cuTensorMapEncodeTiled through the runtime's driver entry point ---------
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool encode_tile_map_2d(CUtensorMap* map, const void* base, bool is_double, uint64_t inner,
+                        uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
+                        uint32_t box_outer) {
+  auto fn = get_encode();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {row_pitch_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, is_double ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// ---- planning -------------------------------------------------------------------
+static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+WavePlan plan_wave(int64_t m, int64_t n, int64_t k, int kmax, int nbt, int K_req, int NB_req,
+                   int elem_bytes) {
+  WavePlan pl{};
+  pl.K = (int)std::min<int64_t>(K_req > 0 ? K_req : kmax, std::min<int64_t>(kmax, k));
+  // The TMA x coordinate of p-block g is 2*g*K elements and must be a multiple
+  // of 16 bytes: for 4-byte elements K must be even once there are two p-blocks.
+  if (elem_bytes == 4 && pl.K < k && (pl.K & 1)) pl.K -= 1;
+  if (pl.K < 1) pl.K = 1;
+  if (elem_bytes == 4 && pl.K < k && (pl.K & 1)) pl.K = 2;
+  pl.NB = NB_req > 0 ? NB_req : 64;
+  if (pl.NB < nbt) pl.NB = nbt;
+  pl.NB = (int)round_up(pl.NB, nbt);
+  pl.delta = 1 + (int)ceil_div(pl.K, pl.NB);
+  pl.nchains = (int)ceil_div(m, 32);
+  pl.G = (int)ceil_div(k, pl.K);
+  pl.B = (int)ceil_div(n + pl.K - 2, pl.NB);
+  pl.total = (long long)pl.nchains * pl.G * pl.B;
+  pl.kpad = (int)std::max<int64_t>(round_up(k, 4), kmax);
+  pl.cs_rows = (int)std::max<int64_t>(n + k - 2, nbt);
+  return pl;
+}
+
+// ---- launch -------------------------------------------------------------------
+template <typename T, int KMAX, int NBT, int WARPS>
+static cudaError_t launch_wave(const WaveProblem& P, const CUtensorMap& map, cudaStream_t stream,
+                               int ctas_per_sm_req) {
+  using SM = WaveSmem<T, KMAX, NBT>;
+  auto kfn = wave_kernel<T, KMAX, NBT, WARPS>;
+  const int smem = WARPS * SM::kWarpBytes;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, WARPS * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  int per_sm = ctas_per_sm_req > 0 ? std::min(ctas_per_sm_req, occ) : occ;
+  long long want = (long long)nsm * per_sm;
+  // No more CTAs than there are items for their warps.
+  long long need = (P.total + WARPS - 1) / WARPS;
+  if (want > need) want = need;
+  if (want < 1) want = 1;
+  kfn<<<(unsigned)want, WARPS * 32, smem, stream>>>(map, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static constexpr int kmax_for() { return 16; }
+static constexpr int kNBT = 16;
+static constexpr int kWarps = 8;
+
+template <typename T>
+rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
+                      const T* S, int64_t lds, cudaStream_t stream, const WaveOptions& opt) {
+  constexpr int KMAX = kmax_for<T>();
+  const WavePlan pl = plan_wave(m, n, k, KMAX, kNBT, opt.K, opt.NB, (int)sizeof(T));
+
+  // Scratch: [repacked (c,s) | done counters | ticket | status]
+  const int64_t W2 = 2 * (int64_t)pl.kpad;
+  const size_t cs_bytes = (size_t)pl.cs_rows * W2 * sizeof(T);
+  const size_t cs_off = 0;
+  const size_t done_off = round_up(cs_bytes, 256);
+  const size_t done_bytes = (size_t)pl.nchains * pl.G * sizeof(int);
+  const size_t tick_off = round_up(done_off + done_bytes, 256);
+  const size_t total_bytes = tick_off + 256;
+
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, total_bytes, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return ROT_ENOMEM;
+  }
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  rot_status st = ROT_OK;
+  do {
+    if (cudaMemsetAsync(base + done_off, 0, total_bytes - done_off, stream) != cudaSuccess) { st = ROT_ECUDA; break; }
+    T* cs = reinterpret_cast<T*>(base + cs_off);
+    dim3 rb(32, 8);
+    dim3 rg((unsigned)ceil_div(n - 1, 32), (unsigned)ceil_div(k, 8));
+    repack_cs_kernel<T><<<rg, rb, 0, stream>>>(C, ldc, S, lds, (int)n, (int)k, cs, W2, 0);
+    if (cudaGetLastError() != cudaSuccess) { st = ROT_ECUDA; break; }
+
+    CUtensorMap map;
+    if (!encode_tile_map_2d(&map, cs, sizeof(T) == 8, (uint64_t)W2, (uint64_t)pl.cs_rows,
+                            (uint64_t)W2 * sizeof(T), 2 * KMAX, kNBT)) { st = ROT_ECUDA; break; }
+
+    WaveProblem P{};
+    P.A = A; P.lda = lda; P.m = (int)m; P.n = (int)n; P.k = (int)k;
+    P.K = pl.K; P.NB = pl.NB; P.delta = pl.delta; P.nchains = pl.nchains; P.G = pl.G; P.B = pl.B;
+    P.cs_row0 = 0;
+    P.done = reinterpret_cast<int*>(base + done_off);
+    P.ticket = reinterpret_cast<unsigned long long*>(base + tick_off);
+    P.status = reinterpret_cast<int*>(base + tick_off + 64);
+    P.total = pl.total;
+    if (launch_wave<T, KMAX, kNBT, kWarps>(P, map, stream, opt.ctas_per_sm) != cudaSuccess) { st = ROT_ECUDA; break; }
+    record_status_async(P.status, stream);
+    if (cudaGetLastError() != cudaSuccess) { st = ROT_ECUDA; break; }
+  } while (0);
+  cudaFreeAsync(scratch, stream);
+  return st;
+}
+
+template rot_status wave_apply<double>(int64_t, int64_t, int64_t, double*, int64_t, const double*,
+                                       int64_t, const double*, int64_t, cudaStream_t,
+                                       const WaveOptions&);
+template rot_status wave_apply<float>(int64_t, int64_t, int64_t, float*, int64_t, const float*,
+                                      int64_t, const float*, int64_t, cudaStream_t,
+                                      const WaveOptions&);
+
+}  // namespace rs

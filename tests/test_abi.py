@@ -1,0 +1,51 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+declared symbol, and rejects bad arguments before touching the device."""
+import ctypes
+
+import pytest
+
+from paper_2412_01852_gb300 import _native, build as _build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return _native.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _native.header_functions()
+    assert "rot_apply" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # every declared function has a binding signature and vice versa
+    assert sorted(_native.SIGNATURES) == names
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        s = lib.rot_status_string(code).decode()
+        assert s.startswith("ROT_")
+    assert lib.rot_version() >= 100
+
+
+P = ctypes.c_void_p(0x1000)  # never dereferenced: validation fails or returns early
+
+
+@pytest.mark.parametrize("fn", ["rot_apply", "rot_apply_f32"])
+@pytest.mark.parametrize("args,code", [
+    ((-1, 4, 2, P, 1, P, 3, P, 3), 1),     # m < 0
+    ((4, -1, 2, P, 4, P, 1, P, 1), 1),     # n < 0
+    ((4, 4, -2, P, 4, P, 3, P, 3), 1),     # k < 0
+    ((4, 4, 2, P, 3, P, 3, P, 3), 1),      # lda < m
+    ((4, 4, 2, P, 4, P, 2, P, 3), 1),      # ldc < n-1
+    ((4, 4, 2, P, 4, P, 3, P, 2), 1),      # lds < n-1
+    ((4, 4, 2, None, 4, P, 3, P, 3), 1),   # NULL A with work
+    ((4, 4, 2, P, 4, None, 3, P, 3), 1),   # NULL C with work
+    ((2**31, 4, 2, P, 2**31, P, 3, P, 3), 1),  # m beyond the limit
+    ((0, 4, 2, None, 1, None, 3, None, 3), 0),   # m == 0: quick return
+    ((4, 1, 2, None, 4, None, 1, None, 1), 0),   # n == 1: quick return
+    ((4, 4, 0, None, 4, None, 3, None, 3), 0),   # k == 0: quick return
+])
+def test_validation_and_quick_return(lib, fn, args, code):
+    assert getattr(lib, fn)(*args, None) == code
