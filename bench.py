@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark of the plain FP64 rotation-sequence path on GB300.
+
+Workload (default "plain-8192"): A is 8192 x 8192 with i.i.d. N(0,1) entries,
+column-major; C, S are 8191 x 192 from angles uniform in [0, 2*pi); seed 2.
+One step = one rot_apply over the whole instance (all 192 sequences of 8191
+rotations applied to all 8192 rows), in place.  A is 512 MiB, larger than the
+129 MB L2, so consecutive steps do not hit in L2.
+
+Metric: rotation-row updates per second (one rotation applied to one row is 6
+flops), whole job over all ranks.  Under torchrun every rank runs its own
+independent instance (seed 2 + rank): weak scaling, no collective on the data
+path.  Prints ONE JSON line on rank 0.
+
+--impl reference times the CPU oracle (plain Algorithm 2 in C, one thread) on
+bounded row samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2412_01852_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "rotation-row updates/s (6 flop each) vs FP64 peak; serving p50/p99 latency"
+# The oracle is run on blocks of this many rows (rows are independent, so any
+# block of rows is a faithful sample of the workload).
+ORACLE_BLOCK = 16
+# FP64 fused multiply-adds per SM per clock: the nominal 1.25 TFLOP/s of GB300
+# divided by (152 SMs x 2 flops x 2.07 GHz) is 1.99, i.e. 2 lanes/clk/SM.
+FP64_FMA_PER_SM_CLK = 2
+UNIT = "rot-rows/s"
+
+# DRAM traffic of one wave-kernel launch on this workload, from the ncu capture
+# summarised in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum),
+# together with a hash of the kernel sources it was taken on.  If the kernel
+# sources change, the number no longer applies and traffic is reported as null.
+# Captured on plain-8192x4096 (4.438e9 B per launch) and scaled by the rotation-rows
+# of plain-8192 (x2.0005): the kernel makes one pass over A per p-block, so its
+# traffic grows with n.
+NCU_TRAFFIC = {"bytes": 8.878e9, "kernel_src_sha": "09fa6569971c4394"}
+
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x20: "sync_boost", 0x40: "sw_thermal_slowdown",
+               0x80: "hw_thermal_slowdown", 0x100: "hw_power_brake_slowdown"}
+
+
+def kernel_src_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("rs_wave.cuh", "rs_device.cuh", "rs_wave_host.cu"):
+        with open(os.path.join(ROOT, "paper_2412_01852_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + SMI_FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 5:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                mask = int(parts[4], 16)
+            except ValueError:
+                continue
+            for bit, name in REASON_BITS.items():
+                if mask & bit and name != "gpu_idle":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def nominal_sm_clock_ghz(dev):
+    """Maximum SM clock of the device in GHz (CUDA attribute, in kHz)."""
+    try:
+        from cuda.bindings import runtime as cr
+        err, khz = cr.cudaDeviceGetAttribute(cr.cudaDeviceAttr.cudaDevAttrClockRate, dev.index)
+        if int(err) == 0 and khz > 0:
+            return khz / 1e6
+    except Exception:
+        pass
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev.index), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=20).stdout.strip()
+        return float(out.splitlines()[0]) / 1e3
+    except Exception:
+        return 2.07
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_leg(cfg, seconds):
+    """The oracle as it stands (one thread) on row blocks of the same instance."""
+    import oracle
+    m, n, k, seed = cfg["m"], cfg["n"], cfg["k"], cfg["seed"]
+    A = wl.matrix(m, n, seed)
+    C, S = wl.rotations(n, k, seed)
+    block = ORACLE_BLOCK
+    rows = 0
+    t0 = time.perf_counter()
+    while rows < m and time.perf_counter() - t0 < seconds:
+        oracle.rot_sequence(A[rows:rows + block], C, S)
+        rows += block
+    el = time.perf_counter() - t0
+    return {"value": rows * (n - 1) * k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "rows 0..%d of the %dx%d, k=%d instance (%d x %d x %d rotation-rows), "
+                      "in blocks of %d rows, plain Algorithm 2 in C, one thread, %.1f s"
+                      % (rows - 1, m, n, k, rows, n - 1, k, ORACLE_BLOCK, el)}
+
+
+def run_reference(args, cfg):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    m, n, k, seed = cfg["m"], cfg["n"], cfg["k"], cfg["seed"]
+    A = wl.matrix(m, n, seed)
+    C, S = wl.rotations(n, k, seed)
+    rows = args.ref_rows
+
+    def one_step(r0):
+        for b in range(r0, r0 + rows, ORACLE_BLOCK):
+            oracle.rot_sequence(A[b:min(b + ORACLE_BLOCK, r0 + rows)], C, S)
+
+    for i in range(args.warmup):
+        one_step(0)
+    times = []
+    for i in range(args.steps):
+        r0 = (i * rows) % (m - rows + 1)
+        t0 = time.perf_counter()
+        one_step(r0)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    work = args.steps * rows * (n - 1) * k
+    value = work / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_block(cfg, ws),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d rows per step of the %dx%d, k=%d instance, in blocks of %d "
+                                   "rows; plain Algorithm 2 in C, one thread" % (rows, m, n, k, ORACLE_BLOCK)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_block(cfg, ws):
+    return {"workload": "%s: A %dx%d N(0,1) column-major, C/S %dx%d from uniform angles, seed %d"
+                        % (cfg["name"], cfg["m"], cfg["n"], cfg["n"] - 1, cfg["k"], cfg["seed"]),
+            "m": cfg["m"], "n": cfg["n"], "k": cfg["k"],
+            "parallelism": "independent instance per rank" if ws > 1 else "single GPU",
+            "l2": "inputs larger than L2 (A is %d MiB)" % (cfg["m"] * cfg["n"] * 8 >> 20)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain-8192")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ref-rows", type=int, default=512)
+    args = ap.parse_args()
+    cfg = dict(wl.WORKLOADS[args.workload])
+    cfg["name"] = args.workload
+
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+    import paper_2412_01852_gb300 as rs
+    from paper_2412_01852_gb300 import api, build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    build.build()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    m, n, k = cfg["m"], cfg["n"], cfg["k"]
+    seed = cfg["seed"] + rank
+    A, C, S = wl.problem(m, n, k, seed)
+    W = wl.rotation_rows(m, n, k)
+    Ad = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()
+    Cd = torch.from_numpy(np.ascontiguousarray(C.T)).to(dev).t()
+    Sd = torch.from_numpy(np.ascontiguousarray(S.T)).to(dev).t()
+    stream = torch.cuda.current_stream()
+
+    peak_gflops, _ = api.measure_fp64_peak()
+
+    for _ in range(args.warmup):
+        rs.rot_apply(Ad, Cd, Sd)
+    torch.cuda.synchronize()
+    rs.rot_device_status()
+
+    # ---- device-timed region ------------------------------------------------------
+    barrier()
+    torch.cuda.synchronize()
+    api.trace_start()
+    l0 = api.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            rs.rot_apply(Ad, Cd, Sd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = api.launch_count() - l0
+    recs = api.trace_stop()
+    rs.rot_device_status()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps * W / (ms * 1e-3)
+
+    wave = [r for r in recs if r[0] == "wave_f64"]
+    kms = sum(r[1] for r in wave) / max(len(wave), 1)
+    achieved_tflops = 6.0 * W / (kms * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    max_clk_ghz = nominal_sm_clock_ghz(dev)
+    peak_tflops = props.multi_processor_count * FP64_FMA_PER_SM_CLK * 2 * max_clk_ghz / 1e3
+    traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["kernel_src_sha"] == kernel_src_sha() else None
+
+    # ---- end to end through the host-buffer entry point ---------------------------
+    Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True)
+    Ah.numpy()[:] = A.T
+    Ch = torch.empty((k, n - 1), dtype=torch.float64, pin_memory=True)
+    Ch.numpy()[:] = C.T
+    Sh = torch.empty((k, n - 1), dtype=torch.float64, pin_memory=True)
+    Sh.numpy()[:] = S.T
+    A_host, C_host, S_host = Ah.numpy().T, Ch.numpy().T, Sh.numpy().T
+    api.rot_apply_host(A_host, C_host, S_host)  # warm-up
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        api.rot_apply_host(A_host, C_host, S_host)
+    el = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([el], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    e2e = {"value": ws * args.e2e_steps * W / el, "unit": UNIT,
+           "h2d_bytes_per_step": int(A.nbytes + C.nbytes + S.nbytes), "d2h_bytes_per_step": int(A.nbytes),
+           "steps": args.e2e_steps}
+
+    cpu = (cpu_baseline_leg(cfg, args.cpu_seconds)
+           if (rank == 0 and ws == 1 and args.cpu_seconds > 0) else None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_block(cfg, ws),
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
+                         "traffic": traffic, "kernel": "wave_kernel<double>",
+                         "kernel_ms": kms,
+                         "peak_source": "nominal FP64 FMA rate: %d SMs x %d DFMA/clk x 2 flops x "
+                                        "%.3f GHz max SM clock" % (props.multi_processor_count,
+                                                                   FP64_FMA_PER_SM_CLK, max_clk_ghz),
+                         "dfma_probe_tflops": peak_gflops / 1e3,
+                         "rotation_ceiling_frac": 0.75},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

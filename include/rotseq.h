@@ -90,6 +90,49 @@ rot_status rot_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda,
                          int64_t ldc, const float* S, int64_t lds, void* stream);
 
 /*
+ * Same computation as rot_apply on HOST buffers: copies A, C and S to the
+ * current device, runs rot_apply on `stream`, copies A back into A_host and
+ * synchronizes `stream` before returning.  Device memory comes from the
+ * stream-ordered allocator and is released before return.  Pinned host
+ * memory gives the fastest copies; pageable memory also works.
+ */
+rot_status rot_apply_host(int64_t m, int64_t n, int64_t k, double* A_host, int64_t lda,
+                          const double* C_host, int64_t ldc, const double* S_host, int64_t lds,
+                          void* stream);
+
+/* ---- measurement ------------------------------------------------------- */
+
+/* One traced kernel launch: its kind, device time and the rotation-row
+ * updates (one rotation applied to one row) it performed. */
+typedef struct {
+  int kind;      /* ROT_KERNEL_* */
+  float ms;      /* CUDA-event time on the launch stream, -1 if unavailable */
+  int64_t work;  /* rotation-row updates done by the launch */
+} rot_trace_record;
+
+enum {
+  ROT_KERNEL_WAVE_F64 = 1,
+  ROT_KERNEL_WAVE_F32 = 2
+};
+
+/* Start recording a CUDA event pair around every main kernel the library
+ * launches (discards earlier records). */
+rot_status rot_trace_start(void);
+
+/* Stop recording; waits for the recorded events, writes up to `capacity`
+ * records to `out` and the number recorded to *count. */
+rot_status rot_trace_stop(rot_trace_record* out, int capacity, int* count);
+
+/* Number of kernels this library has launched in this process. */
+int64_t rot_launch_count(void);
+
+/* FP64 fused multiply-add throughput of the current device, measured by a
+ * short microbenchmark (8 independent DFMA chains per thread, 2 CTAs of 1024
+ * threads per SM): *gflops counts 2 flops per DFMA; *ms (optional) is the
+ * time of one probe launch.  Synchronous. */
+rot_status rot_measure_fp64_peak(double* gflops, double* ms);
+
+/*
  * Synchronizes the current device, then returns and clears the sticky
  * device status: ROT_OK, or ROT_ETIMEOUT if a kernel's bounded wait ran out
  * since the last call, or ROT_ECUDA if the device reported an error.

@@ -28,7 +28,19 @@ SIGNATURES = {
     "rot_apply": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_f32": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_device_status": (ci, []),
+    "rot_apply_host": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "rot_trace_start": (ci, []),
+    "rot_trace_stop": (ci, [vp, ci, ctypes.POINTER(ci)]),
+    "rot_launch_count": (ctypes.c_int64, []),
+    "rot_measure_fp64_peak": (ci, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
+
+
+class TraceRecord(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("ms", ctypes.c_float), ("work", ctypes.c_int64)]
+
+
+KERNEL_KINDS = {1: "wave_f64", 2: "wave_f32"}
 
 
 class RotError(RuntimeError):

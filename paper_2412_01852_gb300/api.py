@@ -82,3 +82,53 @@ def rot_device_status():
     """Synchronize; raise RotError if a kernel recorded a device-side failure."""
     lib = _native.load()
     _native.check(lib.rot_device_status(), "rot_device_status")
+
+
+def rot_apply_host(A, C, S, stream=None):
+    """rot_apply on host numpy arrays (column-major FP64); copies in, runs, copies A back.
+
+    A is updated in place and must be a Fortran-ordered float64 array.
+    """
+    import numpy as np
+    lib = _native.load()
+    for name, a in (("A", A), ("C", C), ("S", S)):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and
+                (a.flags.f_contiguous or a.ndim < 2 or a.shape[0] <= 1)):
+            raise TypeError("%s must be a Fortran-ordered float64 numpy array" % name)
+    m, n = A.shape
+    k = C.shape[1] if C.ndim == 2 else 0
+    nm1 = max(n - 1, 1)
+    _native.check(lib.rot_apply_host(m, n, k, A.ctypes.data or None, max(1, m),
+                                     C.ctypes.data or None, nm1, S.ctypes.data or None, nm1,
+                                     _stream_handle(stream)), "rot_apply_host")
+    return A
+
+
+def trace_start():
+    _native.check(_native.load().rot_trace_start(), "rot_trace_start")
+
+
+def trace_stop(capacity=4096):
+    """Stop tracing; list of (kernel kind name, ms, rotation-row updates)."""
+    import ctypes
+    lib = _native.load()
+    recs = (_native.TraceRecord * capacity)()
+    cnt = ctypes.c_int(0)
+    _native.check(lib.rot_trace_stop(ctypes.cast(recs, ctypes.c_void_p), capacity, ctypes.byref(cnt)),
+                  "rot_trace_stop")
+    return [(_native.KERNEL_KINDS.get(r.kind, str(r.kind)), float(r.ms), int(r.work))
+            for r in recs[:min(cnt.value, capacity)]]
+
+
+def launch_count():
+    return int(_native.load().rot_launch_count())
+
+
+def measure_fp64_peak():
+    """(GFLOP/s counting 2 per DFMA, ms per probe launch) on the current device."""
+    import ctypes
+    g = ctypes.c_double(0)
+    ms = ctypes.c_double(0)
+    _native.check(_native.load().rot_measure_fp64_peak(ctypes.byref(g), ctypes.byref(ms)),
+                  "rot_measure_fp64_peak")
+    return g.value, ms.value

@@ -30,6 +30,11 @@ bool encode_tile_map_2d(CUtensorMap* map, const void* base, bool is_double, uint
                         uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
                         uint32_t box_outer);
 
+// Launch counting and event tracing (rs_util.cu).
+void count_launches(int n);
+int trace_begin(int kind, long long work, cudaStream_t s);
+void trace_end(int id, cudaStream_t s);
+
 // Sticky device status (first error recorded by any launch since the last read).
 int take_sticky_status();
 void record_status_async(const int* status, cudaStream_t stream);

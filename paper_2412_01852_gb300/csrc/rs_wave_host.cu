@@ -150,6 +150,7 @@ rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const 
     dim3 rb(32, 8);
     dim3 rg((unsigned)ceil_div(n - 1, 32), (unsigned)ceil_div(k, 8));
     repack_cs_kernel<T><<<rg, rb, 0, stream>>>(C, ldc, S, lds, (int)n, (int)k, cs, W2, 0);
+    count_launches(1);
     if (cudaGetLastError() != cudaSuccess) { st = ROT_ECUDA; break; }
 
     CUtensorMap map;
@@ -164,8 +165,13 @@ rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const 
     P.ticket = reinterpret_cast<unsigned long long*>(base + tick_off);
     P.status = reinterpret_cast<int*>(base + tick_off + 64);
     P.total = pl.total;
-    if (launch_wave<T, KMAX, kNBT, kWarps>(P, map, stream, opt.ctas_per_sm) != cudaSuccess) { st = ROT_ECUDA; break; }
+    const int tr = trace_begin(sizeof(T) == 8 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32,
+                               (long long)m * (n - 1) * k, stream);
+    const cudaError_t le = launch_wave<T, KMAX, kNBT, kWarps>(P, map, stream, opt.ctas_per_sm);
+    trace_end(tr, stream);
+    if (le != cudaSuccess) { st = ROT_ECUDA; break; }
     record_status_async(P.status, stream);
+    count_launches(2);
     if (cudaGetLastError() != cudaSuccess) { st = ROT_ECUDA; break; }
   } while (0);
   cudaFreeAsync(scratch, stream);

@@ -68,6 +68,8 @@ def problem(m: int, n: int, k: int, seed: int, dtype=np.float64):
 WORKLOADS = {
     "plain-512": dict(m=512, n=512, k=16, seed=1),
     "plain-8192": dict(m=8192, n=8192, k=192, seed=2),
+    # half-width instance of the same rows and sequences, used for profiler captures
+    "plain-8192x4096": dict(m=8192, n=4096, k=192, seed=2),
     "precision-8192": dict(m=8192, n=8192, k=192, seed=2, nb=256, kb=64),
 }
 
