@@ -100,6 +100,34 @@ rot_status rot_apply_host(int64_t m, int64_t n, int64_t k, double* A_host, int64
                           const double* C_host, int64_t ldc, const double* S_host, int64_t lds,
                           void* stream);
 
+/*
+ * rot_apply without any allocation: the same FP64 computation, arguments,
+ * result (bit-identical) and error codes as rot_apply, but its scratch memory
+ * is a fixed 32 MiB static device array inside this library instead of
+ * memory from the CUDA allocator.  The paper has no counterpart; this exists
+ * for callers that cannot let a library allocate device memory -- programs
+ * that reserve the GPU's memory for their own pool up front (or plugins
+ * running inside one), where cudaMalloc would fail or fragment that pool and
+ * its implicit device synchronization would stall their loop.
+ *   Limit: the scratch needed is about 16*(n+k-2)*max(k rounded up to 4, 16)
+ *   bytes for the repacked (c,s) rows plus 4*ceil(m/32)*ceil(k/16) bytes of
+ *   counters (each part rounded up to 256 bytes, plus 256); a problem that
+ *   needs more than 32 MiB is rejected with ROT_EINVAL and nothing is queued.
+ *   (A 8192 x 8192, k = 192 problem needs 24.6 MiB.)
+ *   Every GPU that loads the library keeps the 32 MiB array until the process
+ *   exits.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress, which can load the library's device code); make
+ *   that first call before any stream capture.
+ *   All calls share the one array; the counters are cleared at the start of
+ *   each call, the rest is overwritten.  Calls whose work overlaps on the GPU
+ *   (different streams, or host threads racing on one device) race on it and
+ *   give wrong results: order them on one stream or synchronize in between.
+ */
+rot_status rot_apply_noalloc(int64_t m, int64_t n, int64_t k, double* A, int64_t lda,
+                             const double* C, int64_t ldc, const double* S, int64_t lds,
+                             void* stream);
+
 /* ---- measurement ------------------------------------------------------- */
 
 /* One traced kernel launch: its kind, device time and the rotation-row

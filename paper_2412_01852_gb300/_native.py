@@ -29,6 +29,7 @@ SIGNATURES = {
     "rot_apply_f32": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_device_status": (ci, []),
     "rot_apply_host": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "rot_apply_noalloc": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_trace_start": (ci, []),
     "rot_trace_stop": (ci, [vp, ci, ctypes.POINTER(ci)]),
     "rot_launch_count": (ctypes.c_int64, []),
