@@ -128,6 +128,78 @@ rot_status rot_apply_noalloc(int64_t m, int64_t n, int64_t k, double* A, int64_t
                              const double* C, int64_t ldc, const double* S, int64_t lds,
                              void* stream);
 
+/* ---- batches of independent problems ------------------------------------ */
+
+/* Tiling of the wavefront kernel; 0 in a field means "default" (or the
+ * autotuner's cached choice when a batch plan is created without tuning). */
+typedef struct {
+  int K;            /* sequences fused per work item, 1..16 (default 16) */
+  int NB;           /* waves per work item, rounded up to a multiple of 16 (default 64) */
+  int ctas_per_sm;  /* resident CTAs of 8 warps per SM (default: occupancy limit) */
+} rot_tuning;
+
+/* One FP64 problem of a batch: A (m x n), C and S ((n-1) x k), all device
+ * pointers, column-major, same meaning as rot_apply's arguments. */
+typedef struct {
+  int64_t m, n, k;
+  double* A;
+  int64_t lda;
+  const double* C;
+  int64_t ldc;
+  const double* S;
+  int64_t lds;
+} rot_problem;
+
+typedef struct rot_batch_plan_s rot_batch_plan;
+
+typedef struct {
+  int problems;            /* problems with work (quick-return ones are dropped) */
+  int64_t work_items;      /* (32-row chain, p-block, wave-block) items in the launch */
+  int64_t rotation_rows;   /* sum of m*(n-1)*k */
+  size_t workspace_bytes;  /* device memory the plan holds */
+  rot_tuning tuning;       /* tiling in use */
+} rot_batch_info;
+
+/*
+ * Plan one persistent launch over `count` independent problems (Algorithm 2
+ * for each; rows of different problems never interact).  Every problem is
+ * validated as rot_apply would; any invalid one fails the whole call with
+ * ROT_EINVAL.  The plan allocates one device workspace on the current device
+ * (descriptors, TMA descriptors, the wavefront-ordered work table, counters,
+ * repacked (c,s) rows), uploads the descriptors and returns; it keeps the
+ * problems' device pointers, which must stay valid while the plan is used.
+ * `tuning` may be NULL: the autotuner's cached choice for this batch shape, or
+ * the defaults, are used.  Limits: at most 65535 problems with work.
+ */
+rot_status rot_batch_plan_create(int count, const rot_problem* problems, const rot_tuning* tuning,
+                                 rot_batch_plan** plan);
+
+/* Queue the batch on `stream`: clear counters, repack C/S, one persistent
+ * launch of the wavefront kernel over all problems, fold the status.  No
+ * allocation and no host synchronization, so it can be captured in a CUDA
+ * graph and replayed.  Executions of one plan must not overlap on the GPU. */
+rot_status rot_batch_plan_execute(rot_batch_plan* plan, void* stream);
+
+rot_status rot_batch_plan_info(const rot_batch_plan* plan, rot_batch_info* info);
+
+/* Free the plan (synchronizes the device first: queued work may use it). */
+rot_status rot_batch_plan_destroy(rot_batch_plan* plan);
+
+/* One-shot batch: create a plan, execute it on `stream`, wait, destroy. */
+rot_status rot_apply_batched(int count, const rot_problem* problems, void* stream);
+
+/*
+ * Autotuner: times a small grid of tilings (K in {8,16}, NB in {32,64,128},
+ * CTAs per SM in {1,2}) on scratch copies of the problems' A (so the caller's
+ * data is not modified), stores the fastest in an in-process cache keyed by
+ * the batch's shape signature and the device (and appends it to the file
+ * named by the environment variable ROTSEQ_TUNE_CACHE, if set), and returns
+ * it in *best (and its time in *best_ms, optional).  Synchronous; allocates
+ * the scratch copies from the CUDA allocator.
+ */
+rot_status rot_batch_autotune(int count, const rot_problem* problems, void* stream,
+                              rot_tuning* best, float* best_ms);
+
 /* ---- measurement ------------------------------------------------------- */
 
 /* One traced kernel launch: its kind, device time and the rotation-row
@@ -140,7 +212,8 @@ typedef struct {
 
 enum {
   ROT_KERNEL_WAVE_F64 = 1,
-  ROT_KERNEL_WAVE_F32 = 2
+  ROT_KERNEL_WAVE_F32 = 2,
+  ROT_KERNEL_WAVE_BATCHED = 3
 };
 
 /* Start recording a CUDA event pair around every main kernel the library

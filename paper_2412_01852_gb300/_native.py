@@ -34,14 +34,37 @@ SIGNATURES = {
     "rot_trace_stop": (ci, [vp, ci, ctypes.POINTER(ci)]),
     "rot_launch_count": (ctypes.c_int64, []),
     "rot_measure_fp64_peak": (ci, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "rot_batch_plan_create": (ci, [ci, vp, vp, ctypes.POINTER(vp)]),
+    "rot_batch_plan_execute": (ci, [vp, vp]),
+    "rot_batch_plan_info": (ci, [vp, vp]),
+    "rot_batch_plan_destroy": (ci, [vp]),
+    "rot_apply_batched": (ci, [ci, vp, vp]),
+    "rot_batch_autotune": (ci, [ci, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]),
 }
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("NB", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64),
+                ("S", ctypes.c_void_p), ("lds", ctypes.c_int64)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("problems", ctypes.c_int), ("work_items", ctypes.c_int64),
+                ("rotation_rows", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
+                ("tuning", Tuning)]
 
 
 class TraceRecord(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("ms", ctypes.c_float), ("work", ctypes.c_int64)]
 
 
-KERNEL_KINDS = {1: "wave_f64", 2: "wave_f32"}
+KERNEL_KINDS = {1: "wave_f64", 2: "wave_f32", 3: "wave_batched"}
 
 
 class RotError(RuntimeError):

@@ -132,3 +132,96 @@ def measure_fp64_peak():
     _native.check(_native.load().rot_measure_fp64_peak(ctypes.byref(g), ctypes.byref(ms)),
                   "rot_measure_fp64_peak")
     return g.value, ms.value
+
+
+# ---- batches of independent problems ---------------------------------------------
+
+def _problem_array(problems):
+    arr = (_native.Problem * max(len(problems), 1))()
+    for i, (A, C, S) in enumerate(problems):
+        m, n, k, pa, lda, pc, ldc, ps, lds = _args(A, C, S, torch.float64)
+        arr[i] = _native.Problem(m, n, k, pa, lda, pc, ldc, ps, lds)
+    return arr
+
+
+def _tuning(t):
+    if t is None:
+        return None
+    if isinstance(t, dict):
+        t = (t.get("K", 0), t.get("NB", 0), t.get("ctas_per_sm", 0))
+    return _native.Tuning(*t)
+
+
+class BatchPlan:
+    """One persistent launch over many independent (A, C, S) problems.
+
+    ``problems`` is a list of (A, C, S) column-major FP64 CUDA tensors.  The
+    plan keeps references to them; ``execute`` queues the whole batch on a
+    stream (capturable in a CUDA graph).
+    """
+
+    def __init__(self, problems, tuning=None):
+        import ctypes
+        self._lib = _native.load()
+        self._keep = list(problems)
+        arr = _problem_array(self._keep)
+        h = ctypes.c_void_p()
+        t = _tuning(tuning)
+        _native.check(self._lib.rot_batch_plan_create(
+            len(self._keep), ctypes.cast(arr, ctypes.c_void_p),
+            ctypes.cast(ctypes.pointer(t), ctypes.c_void_p) if t is not None else None,
+            ctypes.byref(h)), "rot_batch_plan_create")
+        self._h = h
+
+    def execute(self, stream=None):
+        _native.check(self._lib.rot_batch_plan_execute(self._h, _stream_handle(stream)),
+                      "rot_batch_plan_execute")
+
+    def info(self):
+        import ctypes
+        inf = _native.BatchInfo()
+        _native.check(self._lib.rot_batch_plan_info(self._h, ctypes.cast(ctypes.pointer(inf), ctypes.c_void_p)),
+                      "rot_batch_plan_info")
+        return {"problems": inf.problems, "work_items": inf.work_items,
+                "rotation_rows": inf.rotation_rows, "workspace_bytes": inf.workspace_bytes,
+                "tuning": {"K": inf.tuning.K, "NB": inf.tuning.NB, "ctas_per_sm": inf.tuning.ctas_per_sm}}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _native.check(self._lib.rot_batch_plan_destroy(self._h), "rot_batch_plan_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rot_apply_batched(problems, stream=None):
+    """Apply every problem's rotations (list of (A, C, S)) in one launch; waits for it."""
+    import ctypes
+    lib = _native.load()
+    arr = _problem_array(problems)
+    _native.check(lib.rot_apply_batched(len(problems), ctypes.cast(arr, ctypes.c_void_p),
+                                        _stream_handle(stream)), "rot_apply_batched")
+
+
+def batch_autotune(problems, stream=None):
+    """Time the tiling grid on copies of the batch; returns (tuning dict, ms)."""
+    import ctypes
+    lib = _native.load()
+    arr = _problem_array(problems)
+    best = _native.Tuning()
+    ms = ctypes.c_float(0)
+    _native.check(lib.rot_batch_autotune(len(problems), ctypes.cast(arr, ctypes.c_void_p),
+                                         _stream_handle(stream),
+                                         ctypes.cast(ctypes.pointer(best), ctypes.c_void_p),
+                                         ctypes.byref(ms)), "rot_batch_autotune")
+    return {"K": best.K, "NB": best.NB, "ctas_per_sm": best.ctas_per_sm}, ms.value

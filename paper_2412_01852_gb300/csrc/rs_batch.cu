@@ -1,0 +1,328 @@
+// rs_batch.cu -- many independent FP64 problems in one persistent launch.
+//
+// A batch plan holds, in one device workspace: the instance descriptors, one
+// TMA descriptor per instance, the segment table that orders every instance's
+// work items by wavefront key, the dependency counters and the repacked (c,s)
+// rows of every instance.  Executing a plan only enqueues kernels (clear the
+// counters, repack C/S, the persistent wave kernel, fold the status), so it
+// can be captured in a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+#include <cuda_runtime.h>
+#include <cuda.h>
+
+#include "rs_wave.cuh"
+#include "rs_internal.h"
+
+namespace rs {
+
+namespace {
+
+constexpr int kKMAX = 16;
+constexpr int kNBT = 16;
+constexpr int kWarps = 8;
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// Where one instance's C and S are and where its repacked rows go.
+struct RepackDesc {
+  const double* C;
+  const double* S;
+  int64_t ldc, lds;
+  double* out;
+  int64_t W2;
+  int n, k;
+  int64_t count;  // (n-1) * k
+};
+
+// One launch repacks every instance: blockIdx.y is the instance, blockIdx.x
+// strides over its (n-1)*k entries.
+__global__ void repack_batch_kernel(const RepackDesc* __restrict__ d, int ninst) {
+  const int i = blockIdx.y;
+  if (i >= ninst) return;
+  const RepackDesc r = d[i];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r.count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % (r.n - 1));
+    const int p = (int)(e / (r.n - 1));
+    double2 v;
+    v.x = r.C[j + (int64_t)p * r.ldc];
+    v.y = r.S[j + (int64_t)p * r.lds];
+    *reinterpret_cast<double2*>(r.out + (int64_t)(j + p) * r.W2 + 2 * p) = v;
+  }
+}
+
+int host_pairs_in_key(int kappa, int G, int B, int delta, int* g_lo) {
+  int hi = kappa / delta;
+  if (hi > G - 1) hi = G - 1;
+  int lo = kappa - (B - 1);
+  lo = lo <= 0 ? 0 : (lo + delta - 1) / delta;
+  *g_lo = lo;
+  return hi >= lo ? hi - lo + 1 : 0;
+}
+
+}  // namespace
+
+struct BatchPlan {
+  int device = 0;
+  int count = 0;          // problems with work
+  rot_tuning tuning{};
+  void* ws = nullptr;     // device workspace (owned)
+  size_t ws_bytes = 0;
+  WaveInstance* d_inst = nullptr;
+  WaveSegment* d_seg = nullptr;
+  RepackDesc* d_rep = nullptr;
+  unsigned char* d_counters = nullptr;  // done counters + ticket + status
+  size_t counters_bytes = 0;
+  WaveLaunch launch{};
+  int nseg = 0;
+  long long total = 0;
+  int repack_grid_x = 1;
+  long long rotation_rows = 0;
+  int grid = 1;           // CTAs of the persistent launch
+  int smem = 0;           // dynamic shared memory per CTA
+};
+
+// Host-side layout of a plan: which problems have work, their tiling, the
+// segment table and the offsets of every part of the workspace.
+struct BatchLayout {
+  std::vector<int> idx;               // problems with work
+  std::vector<WavePlan> wp;           // their tilings
+  std::vector<size_t> cs_off, done_off;
+  std::vector<WaveSegment> seg;
+  size_t done_ints = 0, cs_bytes = 0;
+  size_t o_inst = 0, o_tmap = 0, o_seg = 0, o_rep = 0, o_cnt = 0, o_cs = 0, total = 0;
+  size_t cnt_bytes = 0;
+  long long tickets = 0, rotation_rows = 0;
+};
+
+static rot_status layout_plan(int count, const rot_problem* probs, const rot_tuning& tu,
+                              BatchLayout* L) {
+  const int64_t lim = (int64_t(1) << 31) - 1;
+  for (int i = 0; i < count; ++i) {
+    const rot_problem& q = probs[i];
+    if (q.m < 0 || q.n < 0 || q.k < 0) return ROT_EINVAL;
+    if (q.m > lim || q.n > lim || q.k > lim || q.n + q.k > lim) return ROT_EINVAL;
+    if (q.lda < std::max<int64_t>(1, q.m)) return ROT_EINVAL;
+    const int64_t nm1 = std::max<int64_t>(1, q.n - 1);
+    if (q.ldc < nm1 || q.lds < nm1) return ROT_EINVAL;
+    if (q.m == 0 || q.n <= 1 || q.k == 0) continue;  // quick return: nothing to do
+    if (!q.A || !q.C || !q.S) return ROT_EINVAL;
+    L->idx.push_back(i);
+  }
+  const int ni = (int)L->idx.size();
+  if (ni > 65535) return ROT_EINVAL;  // one grid row per instance in the repack launch
+  L->wp.resize(ni);
+  L->cs_off.resize(ni);
+  L->done_off.resize(ni);
+  int max_key = 0;
+  for (int t = 0; t < ni; ++t) {
+    const rot_problem& q = probs[L->idx[t]];
+    const WavePlan pl = plan_wave(q.m, q.n, q.k, kKMAX, kNBT, tu.K, tu.NB, 8);
+    L->wp[t] = pl;
+    L->done_off[t] = L->done_ints;
+    L->done_ints += (size_t)pl.nchains * pl.G;
+    L->cs_off[t] = L->cs_bytes;
+    L->cs_bytes += round_up((int64_t)pl.cs_rows * 2 * pl.kpad * 8, 256);
+    L->rotation_rows += q.m * (q.n - 1) * q.k;
+    max_key = std::max(max_key, (pl.B - 1) + pl.delta * (pl.G - 1));
+  }
+  // Segment table: keys in increasing order, instances in order within a key.
+  for (int kappa = 0; kappa <= max_key && ni > 0; ++kappa) {
+    for (int t = 0; t < ni; ++t) {
+      int glo;
+      const WavePlan& pl = L->wp[t];
+      const int pairs = host_pairs_in_key(kappa, pl.G, pl.B, pl.delta, &glo);
+      if (pairs <= 0) continue;
+      L->seg.push_back(WaveSegment{L->tickets, t, kappa});
+      L->tickets += (long long)pairs * pl.nchains;
+    }
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes, size_t align) {
+    off = round_up(off, align);
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  L->o_inst = take(sizeof(WaveInstance) * std::max(ni, 1), 256);
+  L->o_tmap = take(sizeof(CUtensorMap) * std::max(ni, 1), 128);
+  L->o_seg = take(sizeof(WaveSegment) * std::max<size_t>(L->seg.size(), 1), 256);
+  L->o_rep = take(sizeof(RepackDesc) * std::max(ni, 1), 256);
+  L->cnt_bytes = round_up(L->done_ints * sizeof(int), 256) + 256;
+  L->o_cnt = take(L->cnt_bytes, 256);
+  L->o_cs = take(L->cs_bytes, 1024);
+  L->total = std::max<size_t>(off, 1024);
+  return ROT_OK;
+}
+
+// Fill the descriptors for a workspace at device address `base` and upload
+// everything that precedes the (c,s) rows.
+static rot_status upload_plan(const BatchLayout& L, const rot_problem* probs, BatchPlan* P) {
+  const int ni = (int)L.idx.size();
+  unsigned char* base = static_cast<unsigned char*>(P->ws);
+  std::vector<unsigned char> img(L.o_cs, 0);
+  WaveInstance* hi = reinterpret_cast<WaveInstance*>(img.data() + L.o_inst);
+  CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(img.data() + L.o_tmap);
+  WaveSegment* hs = reinterpret_cast<WaveSegment*>(img.data() + L.o_seg);
+  RepackDesc* hr = reinterpret_cast<RepackDesc*>(img.data() + L.o_rep);
+  int* d_done = reinterpret_cast<int*>(base + L.o_cnt);
+  int64_t max_count = 1;
+  for (int t = 0; t < ni; ++t) {
+    const rot_problem& q = probs[L.idx[t]];
+    const WavePlan& pl = L.wp[t];
+    double* cs = reinterpret_cast<double*>(base + L.o_cs + L.cs_off[t]);
+    const int64_t W2 = 2 * (int64_t)pl.kpad;
+    if (!encode_tile_map_2d(&ht[t], cs, true, (uint64_t)W2, (uint64_t)pl.cs_rows,
+                            (uint64_t)W2 * sizeof(double), 2 * kKMAX, kNBT))
+      return ROT_ECUDA;
+    WaveInstance I{};
+    I.A = q.A; I.lda = q.lda; I.m = (int)q.m; I.n = (int)q.n; I.k = (int)q.k;
+    I.K = pl.K; I.NB = pl.NB; I.delta = pl.delta; I.nchains = pl.nchains; I.G = pl.G; I.B = pl.B;
+    I.cs_row0 = 0;
+    set_full_range(I);
+    I.done = d_done + L.done_off[t];
+    I.tmap = reinterpret_cast<const CUtensorMap*>(base + L.o_tmap) + t;
+    hi[t] = I;
+    hr[t] = RepackDesc{q.C, q.S, q.ldc, q.lds, cs, W2, (int)q.n, (int)q.k, (q.n - 1) * q.k};
+    max_count = std::max<int64_t>(max_count, hr[t].count);
+  }
+  for (size_t s = 0; s < L.seg.size(); ++s) hs[s] = L.seg[s];
+  if (cudaMemcpy(base, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) return ROT_ECUDA;
+
+  P->count = ni;
+  P->d_inst = reinterpret_cast<WaveInstance*>(base + L.o_inst);
+  P->d_seg = reinterpret_cast<WaveSegment*>(base + L.o_seg);
+  P->d_rep = reinterpret_cast<RepackDesc*>(base + L.o_rep);
+  P->d_counters = base + L.o_cnt;
+  P->counters_bytes = L.cnt_bytes;
+  P->launch.ticket = reinterpret_cast<unsigned long long*>(base + L.o_cnt +
+                                                           round_up(L.done_ints * sizeof(int), 256));
+  P->launch.status = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(P->launch.ticket) + 64);
+  P->launch.total = L.tickets;
+  P->nseg = (int)L.seg.size();
+  P->total = L.tickets;
+  P->rotation_rows = L.rotation_rows;
+  P->repack_grid_x = (int)std::min<int64_t>(ceil_div(max_count, 256), 1024);
+  return ROT_OK;
+}
+
+// Launch geometry of the batched kernel on the current device (set once per
+// plan, so that executing a plan only enqueues stream work).
+static rot_status prepare_launch(BatchPlan* P) {
+  auto kfn = wave_batched_kernel<double, kKMAX, kNBT, kWarps>;
+  const int smem = kWarps * WaveSmem<double, kKMAX, kNBT>::kWarpBytes;
+  if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return ROT_ECUDA;
+  int nsm = 0, occ = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kWarps * 32, smem) != cudaSuccess || occ < 1)
+    return ROT_ECUDA;
+  const int per_sm = P->tuning.ctas_per_sm > 0 ? std::min(P->tuning.ctas_per_sm, occ) : occ;
+  long long grid = (long long)nsm * per_sm;
+  grid = std::min<long long>(grid, (P->total + kWarps - 1) / kWarps);
+  P->grid = (int)std::max<long long>(grid, 1);
+  P->smem = smem;
+  return ROT_OK;
+}
+
+static rot_status execute_plan(BatchPlan* P, cudaStream_t s) {
+  if (P->count == 0) return ROT_OK;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != P->device) return ROT_EINVAL;
+  if (cudaMemsetAsync(P->d_counters, 0, P->counters_bytes, s) != cudaSuccess) return ROT_ECUDA;
+  dim3 rg(P->repack_grid_x, P->count);
+  repack_batch_kernel<<<rg, 256, 0, s>>>(P->d_rep, P->count);
+  if (cudaGetLastError() != cudaSuccess) return ROT_ECUDA;
+  auto kfn = wave_batched_kernel<double, kKMAX, kNBT, kWarps>;
+  const int tr = trace_begin(ROT_KERNEL_WAVE_BATCHED, P->rotation_rows, s);
+  kfn<<<(unsigned)P->grid, kWarps * 32, P->smem, s>>>(P->d_inst, P->d_seg, P->nseg, P->launch);
+  trace_end(tr, s);
+  if (cudaGetLastError() != cudaSuccess) return ROT_ECUDA;
+  record_status_async(P->launch.status, s);
+  if (cudaGetLastError() != cudaSuccess) return ROT_ECUDA;
+  count_launches(3);
+  return ROT_OK;
+}
+
+}  // namespace rs
+
+struct rot_batch_plan_s {
+  rs::BatchPlan p;
+};
+
+extern "C" {
+
+rot_status rot_batch_plan_create(int count, const rot_problem* problems, const rot_tuning* tuning,
+                                 rot_batch_plan** out) {
+  if (!out || count < 0 || (count > 0 && !problems)) return ROT_EINVAL;
+  *out = nullptr;
+  // Validate everything before touching the device.
+  {
+    rs::BatchLayout probe;
+    rot_status v = rs::layout_plan(count, problems, rot_tuning{0, 0, 0}, &probe);
+    if (v != ROT_OK) return v;
+  }
+  rot_tuning tu{};
+  if (tuning) tu = *tuning;
+  else rs::tuning_lookup(count, problems, &tu);
+  if (tu.K < 0 || tu.K > 16 || tu.NB < 0 || tu.NB > 4096 || tu.ctas_per_sm < 0) return ROT_EINVAL;
+  rs::BatchLayout L;
+  rot_status st = rs::layout_plan(count, problems, tu, &L);
+  if (st != ROT_OK) return st;
+  auto* h = new (std::nothrow) rot_batch_plan_s;
+  if (!h) return ROT_ENOMEM;
+  h->p.tuning = tu;
+  h->p.ws_bytes = L.total;
+  if (cudaGetDevice(&h->p.device) != cudaSuccess) { delete h; return ROT_ECUDA; }
+  if (!L.idx.empty()) {
+    if (cudaMalloc(&h->p.ws, h->p.ws_bytes) != cudaSuccess) { cudaGetLastError(); delete h; return ROT_ENOMEM; }
+    st = rs::upload_plan(L, problems, &h->p);
+    if (st == ROT_OK) st = rs::prepare_launch(&h->p);
+    if (st != ROT_OK) { cudaFree(h->p.ws); delete h; return st; }
+  }
+  *out = h;
+  return ROT_OK;
+}
+
+rot_status rot_batch_plan_execute(rot_batch_plan* plan, void* stream) {
+  if (!plan) return ROT_EINVAL;
+  return rs::execute_plan(&plan->p, static_cast<cudaStream_t>(stream));
+}
+
+rot_status rot_batch_plan_info(const rot_batch_plan* plan, rot_batch_info* info) {
+  if (!plan || !info) return ROT_EINVAL;
+  info->problems = plan->p.count;
+  info->work_items = plan->p.total;
+  info->rotation_rows = plan->p.rotation_rows;
+  info->workspace_bytes = plan->p.ws_bytes;
+  info->tuning = plan->p.tuning;
+  return ROT_OK;
+}
+
+rot_status rot_batch_plan_destroy(rot_batch_plan* plan) {
+  if (!plan) return ROT_OK;
+  rot_status st = ROT_OK;
+  if (plan->p.ws) {
+    // The plan's workspace may still be in use by queued work.
+    if (cudaDeviceSynchronize() != cudaSuccess) st = ROT_ECUDA;
+    if (cudaFree(plan->p.ws) != cudaSuccess) st = ROT_ECUDA;
+  }
+  delete plan;
+  return st;
+}
+
+rot_status rot_apply_batched(int count, const rot_problem* problems, void* stream) {
+  rot_batch_plan* plan = nullptr;
+  rot_status st = rot_batch_plan_create(count, problems, nullptr, &plan);
+  if (st != ROT_OK) return st;
+  st = rot_batch_plan_execute(plan, stream);
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess && st == ROT_OK) st = ROT_ECUDA;
+  rot_status d = rot_batch_plan_destroy(plan);
+  return st != ROT_OK ? st : d;
+}
+
+}  // extern "C"

@@ -35,6 +35,10 @@ void count_launches(int n);
 int trace_begin(int kind, long long work, cudaStream_t s);
 void trace_end(int id, cudaStream_t s);
 
+// Autotuner cache (rs_tune.cu): the tiling recorded for a batch of this shape,
+// or the defaults.
+void tuning_lookup(int count, const rot_problem* problems, rot_tuning* out);
+
 // Sticky device status (first error recorded by any launch since the last read).
 int take_sticky_status();
 void record_status_async(const int* status, cudaStream_t stream);

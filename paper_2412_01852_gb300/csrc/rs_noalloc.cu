@@ -116,6 +116,7 @@ extern "C" rot_status rot_apply_noalloc(int64_t m, int64_t n, int64_t k, double*
   P.A = A; P.lda = lda; P.m = (int)m; P.n = (int)n; P.k = (int)k;
   P.K = pl.K; P.NB = pl.NB; P.delta = pl.delta; P.nchains = pl.nchains; P.G = pl.G; P.B = pl.B;
   P.cs_row0 = 0;
+  rs::set_full_range(P);
   P.done = reinterpret_cast<int*>(base + done_off);
   P.ticket = reinterpret_cast<unsigned long long*>(base + tick_off);
   P.status = reinterpret_cast<int*>(base + tick_off + 64);

@@ -54,7 +54,7 @@ __device__ __forceinline__ void rotate(float& x, float& y, float c, float s) {
 }
 
 // One instance of the problem as the wave kernel sees it.
-struct WaveProblem {
+struct WaveInstance {
   void* A;          // column-major m x n, leading dimension lda (elements)
   int64_t lda;
   int m, n, k;
@@ -64,11 +64,42 @@ struct WaveProblem {
   int nchains;      // ceil(m / 32)
   int G;            // p-blocks: ceil(k / K)
   int B;            // wave-blocks of a full p-block: ceil((n + K - 2) / NB)
-  int cs_row0;      // first row of this instance in the repacked (c,s) tensor
+  int cs_row0;      // (c,s) tensor row of rotation (j, p) is cs_row0 + j + p
+  int p_base;       // (c,s) tensor column pair of sequence p is p_base + p
+  int j_lo, j_hi;   // rotations exist for j_lo <= j <= j_hi (normally 0, n-2)
+  int W_lo, W_hi;   // and for j + p in [W_lo, W_hi) (normally everything)
   int* done;        // [nchains * G] completed wave-blocks per (chain, p-block)
+  const void* tmap; // TMA descriptor of the (c,s) tensor (global memory), batched kernel only
+};
+
+// The whole problem: every rotation (j, p) with 0 <= j <= n-2, 0 <= p < k.
+__host__ __device__ inline void set_full_range(WaveInstance& I) {
+  I.p_base = 0;
+  I.j_lo = 0;
+  I.j_hi = I.n - 2;
+  I.W_lo = 0;
+  I.W_hi = 0x7fffffff;
+}
+
+// Kernel-wide state of one launch.
+struct WaveLaunch {
   unsigned long long* ticket;  // next ticket to hand out
-  int* status;      // first device error of this launch (0 = none)
-  long long total;  // nchains * G * B items
+  int* status;                 // first device error of this launch (0 = none)
+  long long total;             // number of tickets
+};
+
+// Backwards-compatible name for the single-instance kernel's parameters.
+struct WaveProblem : WaveInstance {
+  unsigned long long* ticket;
+  int* status;
+  long long total;
+};
+
+// One run of consecutive tickets that belong to one (key, instance).
+struct WaveSegment {
+  long long start;  // first ticket of the run
+  int inst;         // instance index
+  int key;          // key kappa = b + delta * g
 };
 
 // Number of (g, b) pairs whose key b + delta*g equals kappa.
@@ -105,48 +136,188 @@ struct WaveSmem {
   static constexpr int kWarpBytes = 2 * kTileBytes + 128;         // 2 buffers + barriers
 };
 
-// The kernel.  Every warp runs the ticket loop independently; warps of a CTA
-// share nothing but the CTA's shared-memory allocation.
+// Per-warp shared-memory resources: two (c,s) tile buffers and their mbarriers.
+template <typename T, int KMAX, int NBT>
+struct WarpTiles {
+  unsigned char* base;
+  uint64_t* bar;
+  uint32_t phase0, phase1;
+  __device__ __forceinline__ T* tile(int i) const {
+    return reinterpret_cast<T*>(base + i * WaveSmem<T, KMAX, NBT>::kTileBytes);
+  }
+};
+
+template <typename T, int KMAX, int NBT, int WARPS>
+__device__ __forceinline__ WarpTiles<T, KMAX, NBT> warp_tiles_init(unsigned char* smem_raw, int lane) {
+  using SM = WaveSmem<T, KMAX, NBT>;
+  const int warp = threadIdx.x >> 5;
+  WarpTiles<T, KMAX, NBT> wt;
+  wt.base = smem_raw + warp * SM::kWarpBytes;
+  wt.bar = reinterpret_cast<uint64_t*>(wt.base + 2 * SM::kTileBytes);
+  wt.phase0 = 0;
+  wt.phase1 = 0;
+  if (lane == 0) {
+    mbar_init(&wt.bar[0], 1);
+    mbar_init(&wt.bar[1], 1);
+    fence_mbarrier_init();
+  }
+  __syncwarp();
+  return wt;
+}
+
+// Work item (c, g, b) of instance I.  Returns false if the launch must stop
+// (an error was recorded in *status).
+template <typename T, int KMAX, int NBT>
+__device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap, int c, int g,
+                                         int b, WarpTiles<T, KMAX, NBT>& wt, int lane,
+                                         int* status) {
+  using V2 = typename Pair<T>::type;
+  using SM = WaveSmem<T, KMAX, NBT>;
+  const int n = I.n;
+  const int p0 = g * I.K;
+  const int kr = min(I.K, I.k - p0);
+  const int nw = n + kr - 2;                 // waves of this p-block
+  const int w0 = b * I.NB;
+  if (w0 >= nw) return true;                 // empty tail item of a short p-block
+  const int w1 = min(w0 + I.NB, nw);
+  int* const done = I.done + (int64_t)c * I.G;
+
+  // ---- wait for dependencies ------------------------------------------------
+  bool ok = true;
+  if (lane == 0) {
+    if (b > 0) ok = wait_flag_geq(done + g, b, status);
+    if (ok && g > 0) {
+      const int krp = I.K;                   // every p-block but the last is full
+      const int Bp = (n + krp - 2 + I.NB - 1) / I.NB;
+      int need = (w1 + krp + I.NB - 1) / I.NB;
+      if (need > Bp) need = Bp;
+      ok = wait_flag_geq(done + g - 1, need, status);
+    }
+    if (!ok) set_error(status, kDevTimeoutDependency);
+  }
+  ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
+  if (!ok) return false;
+
+  // ---- load the window: columns [w0-kr+1, w0] owned by this p-block ---------
+  const int row = c * 32 + lane;
+  const bool rowok = row < I.m;
+  T* const arow = reinterpret_cast<T*>(I.A) + row;
+  const int64_t lda = I.lda;
+  const int own_lo = w0 - kr + 1;
+  T win[KMAX + 1];
+#pragma unroll
+  for (int s = 0; s < KMAX; ++s) {
+    const int q = w0 + 1 - KMAX + s;
+    win[s] = (rowok && q >= own_lo && q >= 0 && q <= n - 1) ? ld_cg(arow + (int64_t)q * lda) : T(0);
+  }
+  T nextcol = (rowok && w0 + 1 <= n - 1) ? ld_cg(arow + (int64_t)(w0 + 1) * lda) : T(0);
+
+  // Waves of this p-block that hold rotations: the full-sequence wave
+  // j + p = w + p0 must lie in [W_lo, W_hi).
+  const int wr_lo = I.W_lo - p0;
+  const int wr_hi = I.W_hi - p0;
+
+  // ---- stream (c,s) tiles and run the waves ---------------------------------
+  const int ntiles = (w1 - w0 + NBT - 1) / NBT;
+  const int tx = 2 * (I.p_base + p0);
+  const int ty0 = I.cs_row0 + w0 + p0;
+  if (lane == 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&wt.bar[0], SM::kTileBytes);
+    tma_load_2d(wt.tile(0), tmap, &wt.bar[0], tx, ty0);
+  }
+  for (int st = 0; st < ntiles; ++st) {
+    const int cur = st & 1;
+    if (st + 1 < ntiles && lane == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&wt.bar[cur ^ 1], SM::kTileBytes);
+      tma_load_2d(wt.tile(cur ^ 1), tmap, &wt.bar[cur ^ 1], tx, ty0 + (st + 1) * NBT);
+    }
+    const uint32_t ph = cur ? wt.phase1 : wt.phase0;
+    if (!mbar_wait_bounded(&wt.bar[cur], ph)) {
+      if (lane == 0) set_error(status, kDevTimeoutTma);
+      ok = false;
+    }
+    if (cur) wt.phase1 ^= 1u; else wt.phase0 ^= 1u;
+    if (!__all_sync(0xffffffffu, ok)) {
+      // Let the copy already issued into the other buffer land before leaving.
+      if (st + 1 < ntiles) (void)mbar_wait_bounded(&wt.bar[cur ^ 1], cur ? wt.phase0 : wt.phase1);
+      return false;
+    }
+    const V2* tl = reinterpret_cast<const V2*>(wt.tile(cur));
+    const int ws = w0 + st * NBT;
+    const int wend = min(ws + NBT, w1);
+    for (int w = ws; w < wend; ++w) {
+      win[KMAX] = nextcol;
+      nextcol = (rowok && w + 2 <= n - 1) ? ld_cg(arow + (int64_t)(w + 2) * lda) : T(0);
+      // Rotations l = l_lo..l_hi in increasing l, j = w - l in [j_lo, j_hi].
+      // The bounds are the same for all lanes, so the early exit is a
+      // uniform branch and a short p-block issues only its own kr rotations.
+      const int l_lo = max(0, w - I.j_hi);
+      const int l_hi = (w >= wr_lo && w < wr_hi) ? min(kr - 1, w - I.j_lo) : -1;
+      const V2* trow = tl + (w - ws) * KMAX;
+#pragma unroll
+      for (int l = 0; l < KMAX; ++l) {
+        if (l > l_hi) break;
+        if (l >= l_lo) {
+          const V2 cs = trow[l];
+          rotate(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
+        }
+      }
+      const int q = w + 1 - KMAX;            // column leaving the window
+      if (rowok && q >= own_lo && q >= 0) st_cg(arow + (int64_t)q * lda, win[0]);
+#pragma unroll
+      for (int s = 0; s < KMAX; ++s) win[s] = win[s + 1];
+    }
+    __syncwarp();
+  }
+
+  // ---- flush the window: columns [w1+1-KMAX, w1] ----------------------------
+#pragma unroll
+  for (int s = 0; s < KMAX; ++s) {
+    const int q = w1 + 1 - KMAX + s;
+    if (rowok && q >= own_lo && q >= 0 && q <= n - 1) st_cg(arow + (int64_t)q * lda, win[s]);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence();
+    st_release_gpu(done + g, b + 1);
+  }
+  return true;
+}
+
+// Hand out the next ticket to the whole warp; -1 when the launch is over.
+__device__ __forceinline__ long long next_ticket(unsigned long long* ticket, long long total,
+                                                 const int* status, int lane) {
+  long long t = 0;
+  if (lane == 0) {
+    t = (long long)atomicAdd(ticket, 1ull);
+    if (t >= total || ld_relaxed_gpu(status) != 0) t = -1;
+  }
+  return __shfl_sync(0xffffffffu, t, 0);
+}
+
+// Single instance: tickets decode in closed form (keys b + delta*g, within a
+// key p-block-major then chain-minor).  Every warp runs the ticket loop
+// independently; warps of a CTA share nothing but the CTA's shared memory.
 template <typename T, int KMAX, int NBT, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 wave_kernel(const __grid_constant__ CUtensorMap tmap, const WaveProblem P) {
-  using V2 = typename Pair<T>::type;
-  using SM = WaveSmem<T, KMAX, NBT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  unsigned char* wbase = smem_raw + warp * SM::kWarpBytes;
-  auto tile = [&](int i) { return reinterpret_cast<T*>(wbase + i * SM::kTileBytes); };
-  uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + 2 * SM::kTileBytes);
-
-  if (lane == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbarrier_init();
-    prefetch_tmap(&tmap);
-  }
-  __syncwarp();
-  uint32_t phase0 = 0, phase1 = 0;
+  auto wt = warp_tiles_init<T, KMAX, NBT, WARPS>(smem_raw, lane);
+  if (lane == 0) prefetch_tmap(&tmap);
 
   // Ticket -> key cursor (tickets a warp receives only increase).
   int kappa = 0;
   long long kstart = 0;
   int kglo = 0;
   int kcount = pairs_in_key(0, P.G, P.B, P.delta, &kglo) * P.nchains;
-
-  T* const A = reinterpret_cast<T*>(P.A);
-  const int n = P.n;
+  const int last_key = (P.B - 1) + P.delta * (P.G - 1);
 
   while (true) {
-    long long t = 0;
-    if (lane == 0) t = (long long)atomicAdd(P.ticket, 1ull);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= P.total) break;
-    if (lane == 0 && ld_relaxed_gpu(P.status) != 0) t = -1;
-    t = __shfl_sync(0xffffffffu, t, 0);
+    const long long t = next_ticket(P.ticket, P.total, P.status, lane);
     if (t < 0) break;
-
-    const int last_key = (P.B - 1) + P.delta * (P.G - 1);
     while (t >= kstart + kcount && kappa <= last_key) {
       kstart += kcount;
       ++kappa;
@@ -161,112 +332,39 @@ wave_kernel(const __grid_constant__ CUtensorMap tmap, const WaveProblem P) {
     const int c = (int)(r - (long long)gi * P.nchains);
     const int g = kglo + gi;
     const int b = kappa - P.delta * g;
-    const int p0 = g * P.K;
-    const int kr = min(P.K, P.k - p0);
-    const int nw = n + kr - 2;                 // waves of this p-block
-    const int w0 = b * P.NB;
-    if (w0 >= nw) continue;                    // empty tail item of a short p-block
-    const int w1 = min(w0 + P.NB, nw);
-    int* const done = P.done + (int64_t)c * P.G;
+    if (!run_item<T, KMAX, NBT>(P, &tmap, c, g, b, wt, lane, P.status)) break;
+  }
+}
 
-    // ---- wait for dependencies ------------------------------------------------
-    bool ok = true;
-    if (lane == 0) {
-      if (b > 0) ok = wait_flag_geq(done + g, b, P.status);
-      if (ok && g > 0) {
-        const int krp = P.K;                   // every p-block but the last is full
-        const int nwp = n + krp - 2;
-        const int Bp = (nwp + P.NB - 1) / P.NB;
-        int need = (w1 + krp + P.NB - 1) / P.NB;
-        if (need > Bp) need = Bp;
-        ok = wait_flag_geq(done + g - 1, need, P.status);
-      }
-      if (!ok) set_error(P.status, kDevTimeoutDependency);
+// Many instances in one launch: tickets run through a host-built table of
+// segments (key, instance, first ticket), ordered by key and then instance,
+// so that every dependency of an item has a smaller ticket.
+template <typename T, int KMAX, int NBT, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+wave_batched_kernel(const WaveInstance* __restrict__ insts, const WaveSegment* __restrict__ segs,
+                    int nseg, const WaveLaunch L) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  auto wt = warp_tiles_init<T, KMAX, NBT, WARPS>(smem_raw, lane);
+  int s = 0;
+  while (true) {
+    const long long t = next_ticket(L.ticket, L.total, L.status, lane);
+    if (t < 0) break;
+    while (s + 1 < nseg && t >= segs[s + 1].start) ++s;
+    const WaveSegment sg = segs[s];
+    const WaveInstance I = insts[sg.inst];
+    int glo = 0;
+    const int npairs = pairs_in_key(sg.key, I.G, I.B, I.delta, &glo);
+    const long long r = t - sg.start;
+    const int gi = (int)(r / I.nchains);
+    if (gi >= npairs || t < sg.start) {        // cannot happen: segments cover every ticket
+      if (lane == 0) set_error(L.status, kDevBadItem);
+      break;
     }
-    ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
-    if (!ok) break;
-
-    // ---- load the window: columns [w0-kr+1, w0] owned by this p-block ---------
-    const int row = c * 32 + lane;
-    const bool rowok = row < P.m;
-    T* const arow = A + row;
-    const int own_lo = w0 - kr + 1;
-    T win[KMAX + 1];
-#pragma unroll
-    for (int s = 0; s < KMAX; ++s) {
-      const int q = w0 + 1 - KMAX + s;
-      win[s] = (rowok && q >= own_lo && q >= 0 && q <= n - 1) ? ld_cg(arow + (int64_t)q * P.lda) : T(0);
-    }
-    T nextcol = (rowok && w0 + 1 <= n - 1) ? ld_cg(arow + (int64_t)(w0 + 1) * P.lda) : T(0);
-
-    // ---- stream (c,s) tiles and run the waves ---------------------------------
-    const int ntiles = (w1 - w0 + NBT - 1) / NBT;
-    const int tx = 2 * p0;
-    const int ty0 = P.cs_row0 + w0 + p0;
-    if (lane == 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bar[0], SM::kTileBytes);
-      tma_load_2d(tile(0), &tmap, &bar[0], tx, ty0);
-    }
-    for (int st = 0; st < ntiles; ++st) {
-      const int cur = st & 1;
-      if (st + 1 < ntiles && lane == 0) {
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar[cur ^ 1], SM::kTileBytes);
-        tma_load_2d(tile(cur ^ 1), &tmap, &bar[cur ^ 1], tx, ty0 + (st + 1) * NBT);
-      }
-      const uint32_t ph = cur ? phase1 : phase0;
-      if (!mbar_wait_bounded(&bar[cur], ph)) {
-        if (lane == 0) set_error(P.status, kDevTimeoutTma);
-        ok = false;
-      }
-      if (cur) phase1 ^= 1u; else phase0 ^= 1u;
-      if (!__all_sync(0xffffffffu, ok)) {
-        // Let the copy already issued into the other buffer land before leaving.
-        if (st + 1 < ntiles) (void)mbar_wait_bounded(&bar[cur ^ 1], cur ? phase0 : phase1);
-        ok = false;
-        break;
-      }
-      const V2* tl = reinterpret_cast<const V2*>(tile(cur));
-      const int ws = w0 + st * NBT;
-      const int wend = min(ws + NBT, w1);
-      for (int w = ws; w < wend; ++w) {
-        win[KMAX] = nextcol;
-        nextcol = (rowok && w + 2 <= n - 1) ? ld_cg(arow + (int64_t)(w + 2) * P.lda) : T(0);
-        const int l_lo = max(0, w - (n - 2));
-        const int l_hi = min(kr - 1, w);
-        const V2* trow = tl + (w - ws) * KMAX;
-        // Rotations l = l_lo..l_hi in increasing l.  The bounds are the same
-        // for all lanes, so the early exit is a uniform branch and a short
-        // p-block issues only its own kr rotations.
-#pragma unroll
-        for (int l = 0; l < KMAX; ++l) {
-          if (l > l_hi) break;
-          if (l >= l_lo) {
-            const V2 cs = trow[l];
-            rotate(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
-          }
-        }
-        const int q = w + 1 - KMAX;            // column leaving the window
-        if (rowok && q >= own_lo && q >= 0) st_cg(arow + (int64_t)q * P.lda, win[0]);
-#pragma unroll
-        for (int s = 0; s < KMAX; ++s) win[s] = win[s + 1];
-      }
-      __syncwarp();
-    }
-    if (!ok) break;
-
-    // ---- flush the window: columns [w1+1-KMAX, w1] ----------------------------
-#pragma unroll
-    for (int s = 0; s < KMAX; ++s) {
-      const int q = w1 + 1 - KMAX + s;
-      if (rowok && q >= own_lo && q >= 0 && q <= n - 1) st_cg(arow + (int64_t)q * P.lda, win[s]);
-    }
-    __syncwarp();
-    if (lane == 0) {
-      __threadfence();
-      st_release_gpu(done + g, b + 1);
-    }
+    const int c = (int)(r - (long long)gi * I.nchains);
+    const int g = glo + gi;
+    const int b = sg.key - I.delta * g;
+    if (!run_item<T, KMAX, NBT>(I, I.tmap, c, g, b, wt, lane, L.status)) break;
   }
 }
 

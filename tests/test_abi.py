@@ -49,3 +49,23 @@ P = ctypes.c_void_p(0x1000)  # never dereferenced: validation fails or returns e
 ])
 def test_validation_and_quick_return(lib, fn, args, code):
     assert getattr(lib, fn)(*args, None) == code
+
+
+def test_batch_plan_rejects_invalid_problems(lib):
+    """Invalid problems fail the whole plan before any device work."""
+    from paper_2412_01852_gb300 import _native as nat
+    arr = (nat.Problem * 3)()
+    arr[0] = nat.Problem(4, 4, 2, 0x1000, 4, 0x1000, 3, 0x1000, 3)
+    arr[1] = nat.Problem(4, 4, 2, 0x1000, 3, 0x1000, 3, 0x1000, 3)   # lda < m
+    arr[2] = nat.Problem(0, 4, 2, 0, 1, 0, 3, 0, 3)                  # quick return
+    h = ctypes.c_void_p()
+    assert lib.rot_batch_plan_create(3, ctypes.cast(arr, ctypes.c_void_p), None, ctypes.byref(h)) == 1
+    assert lib.rot_batch_plan_create(-1, None, None, ctypes.byref(h)) == 1
+    assert lib.rot_batch_plan_create(1, None, None, ctypes.byref(h)) == 1
+    bad = nat.Tuning(17, 64, 0)
+    arr2 = (nat.Problem * 1)()
+    arr2[0] = nat.Problem(4, 4, 2, 0x1000, 4, 0x1000, 3, 0x1000, 3)
+    assert lib.rot_batch_plan_create(1, ctypes.cast(arr2, ctypes.c_void_p),
+                                     ctypes.cast(ctypes.pointer(bad), ctypes.c_void_p),
+                                     ctypes.byref(h)) == 1
+    assert lib.rot_batch_plan_destroy(None) == 0
