@@ -200,6 +200,71 @@ rot_status rot_apply_batched(int count, const rot_problem* problems, void* strea
 rot_status rot_batch_autotune(int count, const rot_problem* problems, void* stream,
                               rot_tuning* best, float* best_ms);
 
+/* ---- serving: continuous batching of requests on resident matrices ------ */
+
+typedef struct rot_server_s rot_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;  /* device memory reserved up front for request
+                               workspaces (C, S and the launch's working
+                               buffers); at least 1 MiB */
+  int max_inflight;         /* requests admitted and not yet complete */
+  int streams;              /* launches that may run at the same time, 1..64 */
+  int max_batch;            /* requests per launch */
+} rot_server_config;
+
+typedef struct {
+  int64_t completed, rejected, pending, inflight, launches;
+  double mean_batch;            /* requests per launch */
+  double p50_ms, p99_ms, max_ms;/* submit-to-completion latency */
+  int64_t rotation_rows;        /* of the completed requests */
+  double busy_s;                /* first submit to last completion */
+  double rotation_rows_per_s;   /* rotation_rows / busy_s */
+  size_t arena_used_bytes;      /* workspace memory in use now */
+} rot_server_stats_t;
+
+/*
+ * Start a server on the current device: reserves cfg->hbm_budget_bytes of
+ * device memory as its workspace arena, creates cfg->streams streams and a
+ * scheduler thread.  Each scheduling step admits pending requests in
+ * submission order while a request slot (max_inflight) and arena memory are
+ * free, puts everything admitted in that step (at most max_batch) into one
+ * launch of the batched wavefront kernel, and issues it on a free stream;
+ * launches on different streams overlap on the device.  A matrix is never in
+ * two launches at once, so requests on one matrix apply in submission order.
+ * The paper has no serving layer; every request computes Algorithm 2 on its
+ * matrix exactly as rot_apply would (bit-identical results).
+ */
+rot_status rot_server_create(const rot_server_config* cfg, rot_server** server);
+
+/* Register a resident device matrix A (m x n, lda), owned by the caller, which
+ * must keep it alive and not touch it while requests on it are in flight. */
+rot_status rot_server_register(rot_server* server, int64_t m, int64_t n, double* A, int64_t lda,
+                               int* handle);
+
+/*
+ * Submit a request: apply the k sequences in host arrays C_host, S_host
+ * ((n-1) x k, column-major, leading dimensions ldc, lds) to matrix `handle`.
+ * C and S are copied before return.  Non-blocking; *ticket identifies the
+ * request for rot_server_wait.  ROT_ENOMEM if the request could never fit in
+ * the arena; ROT_EINVAL for bad arguments or after destroy began.
+ */
+rot_status rot_server_submit(rot_server* server, int handle, int64_t k, const double* C_host,
+                             int64_t ldc, const double* S_host, int64_t lds, uint64_t* ticket);
+
+/* Wait for a request (timeout_ms < 0: no limit).  Returns the request's
+ * status (ROT_OK, or ROT_ETIMEOUT if its launch reported a device-side wait
+ * that ran out), or ROT_ETIMEOUT if the wait itself ran out (the request is
+ * still live and can be waited on again).  A ticket can be waited on until it
+ * has returned its status once. */
+rot_status rot_server_wait(rot_server* server, uint64_t ticket, int timeout_ms);
+
+/* Statistics since creation or the last reset (reset != 0 clears them). */
+rot_status rot_server_stats(rot_server* server, rot_server_stats_t* stats, int reset);
+
+/* Drain every submitted request, stop the scheduler and free the server. */
+rot_status rot_server_destroy(rot_server* server);
+
 /* ---- measurement ------------------------------------------------------- */
 
 /* One traced kernel launch: its kind, device time and the rotation-row

@@ -40,7 +40,27 @@ SIGNATURES = {
     "rot_batch_plan_destroy": (ci, [vp]),
     "rot_apply_batched": (ci, [ci, vp, vp]),
     "rot_batch_autotune": (ci, [ci, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]),
+    "rot_server_create": (ci, [vp, ctypes.POINTER(vp)]),
+    "rot_server_register": (ci, [vp, i64, i64, vp, i64, ctypes.POINTER(ci)]),
+    "rot_server_submit": (ci, [vp, ci, i64, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_uint64)]),
+    "rot_server_wait": (ci, [vp, ctypes.c_uint64, ci]),
+    "rot_server_stats": (ci, [vp, vp, ci]),
+    "rot_server_destroy": (ci, [vp]),
 }
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
+                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("inflight", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("mean_batch", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("rotation_rows", ctypes.c_int64), ("busy_s", ctypes.c_double),
+                ("rotation_rows_per_s", ctypes.c_double), ("arena_used_bytes", ctypes.c_size_t)]
 
 
 class Tuning(ctypes.Structure):

@@ -225,3 +225,78 @@ def batch_autotune(problems, stream=None):
                                          ctypes.cast(ctypes.pointer(best), ctypes.c_void_p),
                                          ctypes.byref(ms)), "rot_batch_autotune")
     return {"K": best.K, "NB": best.NB, "ctas_per_sm": best.ctas_per_sm}, ms.value
+
+
+# ---- serving -----------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching server over resident device matrices (rot_server_* in the C ABI).
+
+    ``register(A)`` takes a column-major FP64 CUDA tensor that stays resident;
+    ``submit(handle, C, S)`` takes host numpy arrays ((n-1) x k, FP64) and
+    returns a ticket; ``wait(ticket, timeout_ms)`` returns when the request is
+    done (raises RotError on failure, including a wait that runs out).
+    """
+
+    def __init__(self, hbm_budget_bytes=1 << 30, max_inflight=64, streams=4, max_batch=32):
+        import ctypes
+        self._lib = _native.load()
+        cfg = _native.ServerConfig(int(hbm_budget_bytes), int(max_inflight), int(streams), int(max_batch))
+        h = ctypes.c_void_p()
+        _native.check(self._lib.rot_server_create(ctypes.cast(ctypes.pointer(cfg), ctypes.c_void_p),
+                                                  ctypes.byref(h)), "rot_server_create")
+        self._h = h
+        self._mats = []
+
+    def register(self, A):
+        import ctypes
+        m, n = A.shape
+        h = ctypes.c_int(-1)
+        _native.check(self._lib.rot_server_register(self._h, m, n, A.data_ptr(), _ld(A, m),
+                                                    ctypes.byref(h)), "rot_server_register")
+        self._mats.append(A)  # keep the tensor alive while the server may use it
+        return h.value
+
+    def submit(self, handle, C, S):
+        import ctypes
+        import numpy as np
+        C = np.asfortranarray(C, dtype=np.float64)
+        S = np.asfortranarray(S, dtype=np.float64)
+        if C.shape != S.shape or C.ndim != 2:
+            raise ValueError("C and S must be (n-1) x k arrays")
+        t = ctypes.c_uint64(0)
+        _native.check(self._lib.rot_server_submit(self._h, int(handle), C.shape[1], C.ctypes.data,
+                                                  max(1, C.shape[0]), S.ctypes.data, max(1, S.shape[0]),
+                                                  ctypes.byref(t)), "rot_server_submit")
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        _native.check(self._lib.rot_server_wait(self._h, int(ticket), int(timeout_ms)), "rot_server_wait")
+
+    def try_wait(self, ticket, timeout_ms=0):
+        """Status code of the wait (0 = done and ok) instead of raising."""
+        return int(self._lib.rot_server_wait(self._h, int(ticket), int(timeout_ms)))
+
+    def stats(self, reset=False):
+        import ctypes
+        st = _native.ServerStats()
+        _native.check(self._lib.rot_server_stats(self._h, ctypes.cast(ctypes.pointer(st), ctypes.c_void_p),
+                                                 1 if reset else 0), "rot_server_stats")
+        return {f: getattr(st, f) for f, _ in _native.ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _native.check(self._lib.rot_server_destroy(self._h), "rot_server_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -13,8 +13,7 @@
 #include <cuda_runtime.h>
 #include <cuda.h>
 
-#include "rs_wave.cuh"
-#include "rs_internal.h"
+#include "rs_batch.h"
 
 namespace rs {
 
@@ -66,41 +65,7 @@ int host_pairs_in_key(int kappa, int G, int B, int delta, int* g_lo) {
 
 }  // namespace
 
-struct BatchPlan {
-  int device = 0;
-  int count = 0;          // problems with work
-  rot_tuning tuning{};
-  void* ws = nullptr;     // device workspace (owned)
-  size_t ws_bytes = 0;
-  WaveInstance* d_inst = nullptr;
-  WaveSegment* d_seg = nullptr;
-  RepackDesc* d_rep = nullptr;
-  unsigned char* d_counters = nullptr;  // done counters + ticket + status
-  size_t counters_bytes = 0;
-  WaveLaunch launch{};
-  int nseg = 0;
-  long long total = 0;
-  int repack_grid_x = 1;
-  long long rotation_rows = 0;
-  int grid = 1;           // CTAs of the persistent launch
-  int smem = 0;           // dynamic shared memory per CTA
-};
-
-// Host-side layout of a plan: which problems have work, their tiling, the
-// segment table and the offsets of every part of the workspace.
-struct BatchLayout {
-  std::vector<int> idx;               // problems with work
-  std::vector<WavePlan> wp;           // their tilings
-  std::vector<size_t> cs_off, done_off;
-  std::vector<WaveSegment> seg;
-  size_t done_ints = 0, cs_bytes = 0;
-  size_t o_inst = 0, o_tmap = 0, o_seg = 0, o_rep = 0, o_cnt = 0, o_cs = 0, total = 0;
-  size_t cnt_bytes = 0;
-  long long tickets = 0, rotation_rows = 0;
-};
-
-static rot_status layout_plan(int count, const rot_problem* probs, const rot_tuning& tu,
-                              BatchLayout* L) {
+rot_status batch_layout(int count, const rot_problem* probs, const rot_tuning& tu, BatchLayout* L) {
   const int64_t lim = (int64_t(1) << 31) - 1;
   for (int i = 0; i < count; ++i) {
     const rot_problem& q = probs[i];
@@ -159,16 +124,14 @@ static rot_status layout_plan(int count, const rot_problem* probs, const rot_tun
   return ROT_OK;
 }
 
-// Fill the descriptors for a workspace at device address `base` and upload
-// everything that precedes the (c,s) rows.
-static rot_status upload_plan(const BatchLayout& L, const rot_problem* probs, BatchPlan* P) {
+rot_status batch_image(const BatchLayout& L, const rot_problem* probs, unsigned char* base,
+                       unsigned char* img, BatchLaunch* B) {
   const int ni = (int)L.idx.size();
-  unsigned char* base = static_cast<unsigned char*>(P->ws);
-  std::vector<unsigned char> img(L.o_cs, 0);
-  WaveInstance* hi = reinterpret_cast<WaveInstance*>(img.data() + L.o_inst);
-  CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(img.data() + L.o_tmap);
-  WaveSegment* hs = reinterpret_cast<WaveSegment*>(img.data() + L.o_seg);
-  RepackDesc* hr = reinterpret_cast<RepackDesc*>(img.data() + L.o_rep);
+  std::memset(img, 0, L.o_cs);
+  WaveInstance* hi = reinterpret_cast<WaveInstance*>(img + L.o_inst);
+  CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(img + L.o_tmap);
+  WaveSegment* hs = reinterpret_cast<WaveSegment*>(img + L.o_seg);
+  RepackDesc* hr = reinterpret_cast<RepackDesc*>(img + L.o_rep);
   int* d_done = reinterpret_cast<int*>(base + L.o_cnt);
   int64_t max_count = 1;
   for (int t = 0; t < ni; ++t) {
@@ -190,59 +153,59 @@ static rot_status upload_plan(const BatchLayout& L, const rot_problem* probs, Ba
     hr[t] = RepackDesc{q.C, q.S, q.ldc, q.lds, cs, W2, (int)q.n, (int)q.k, (q.n - 1) * q.k};
     max_count = std::max<int64_t>(max_count, hr[t].count);
   }
-  for (size_t s = 0; s < L.seg.size(); ++s) hs[s] = L.seg[s];
-  if (cudaMemcpy(base, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) return ROT_ECUDA;
+  for (size_t i = 0; i < L.seg.size(); ++i) hs[i] = L.seg[i];
 
-  P->count = ni;
-  P->d_inst = reinterpret_cast<WaveInstance*>(base + L.o_inst);
-  P->d_seg = reinterpret_cast<WaveSegment*>(base + L.o_seg);
-  P->d_rep = reinterpret_cast<RepackDesc*>(base + L.o_rep);
-  P->d_counters = base + L.o_cnt;
-  P->counters_bytes = L.cnt_bytes;
-  P->launch.ticket = reinterpret_cast<unsigned long long*>(base + L.o_cnt +
+  B->count = ni;
+  B->base = base;
+  B->bytes = L.total;
+  B->d_inst = reinterpret_cast<WaveInstance*>(base + L.o_inst);
+  B->d_seg = reinterpret_cast<WaveSegment*>(base + L.o_seg);
+  B->d_rep = base + L.o_rep;
+  B->d_counters = base + L.o_cnt;
+  B->counters_bytes = L.cnt_bytes;
+  B->launch.ticket = reinterpret_cast<unsigned long long*>(base + L.o_cnt +
                                                            round_up(L.done_ints * sizeof(int), 256));
-  P->launch.status = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(P->launch.ticket) + 64);
-  P->launch.total = L.tickets;
-  P->nseg = (int)L.seg.size();
-  P->total = L.tickets;
-  P->rotation_rows = L.rotation_rows;
-  P->repack_grid_x = (int)std::min<int64_t>(ceil_div(max_count, 256), 1024);
+  B->launch.status = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(B->launch.ticket) + 64);
+  B->launch.total = L.tickets;
+  B->nseg = (int)L.seg.size();
+  B->total = L.tickets;
+  B->rotation_rows = L.rotation_rows;
+  B->repack_grid_x = (int)std::min<int64_t>(ceil_div(max_count, 256), 1024);
   return ROT_OK;
 }
 
-// Launch geometry of the batched kernel on the current device (set once per
-// plan, so that executing a plan only enqueues stream work).
-static rot_status prepare_launch(BatchPlan* P) {
+rot_status batch_prepare(BatchLaunch* B) {
   auto kfn = wave_batched_kernel<double, kKMAX, kNBT, kWarps>;
   const int smem = kWarps * WaveSmem<double, kKMAX, kNBT>::kWarpBytes;
+  if (cudaGetDevice(&B->device) != cudaSuccess) return ROT_ECUDA;
   if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return ROT_ECUDA;
   int nsm = 0, occ = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B->device);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kWarps * 32, smem) != cudaSuccess || occ < 1)
     return ROT_ECUDA;
-  const int per_sm = P->tuning.ctas_per_sm > 0 ? std::min(P->tuning.ctas_per_sm, occ) : occ;
+  const int per_sm = B->tuning.ctas_per_sm > 0 ? std::min(B->tuning.ctas_per_sm, occ) : occ;
   long long grid = (long long)nsm * per_sm;
-  grid = std::min<long long>(grid, (P->total + kWarps - 1) / kWarps);
-  P->grid = (int)std::max<long long>(grid, 1);
-  P->smem = smem;
+  grid = std::min<long long>(grid, (B->total + kWarps - 1) / kWarps);
+  B->grid = (int)std::max<long long>(grid, 1);
+  B->smem = smem;
   return ROT_OK;
 }
 
-static rot_status execute_plan(BatchPlan* P, cudaStream_t s) {
-  if (P->count == 0) return ROT_OK;
+rot_status batch_enqueue(const BatchLaunch& B, cudaStream_t s) {
+  if (B.count == 0) return ROT_OK;
   int cur = 0;
-  if (cudaGetDevice(&cur) != cudaSuccess || cur != P->device) return ROT_EINVAL;
-  if (cudaMemsetAsync(P->d_counters, 0, P->counters_bytes, s) != cudaSuccess) return ROT_ECUDA;
-  dim3 rg(P->repack_grid_x, P->count);
-  repack_batch_kernel<<<rg, 256, 0, s>>>(P->d_rep, P->count);
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != B.device) return ROT_EINVAL;
+  if (cudaMemsetAsync(B.d_counters, 0, B.counters_bytes, s) != cudaSuccess) return ROT_ECUDA;
+  dim3 rg(B.repack_grid_x, B.count);
+  repack_batch_kernel<<<rg, 256, 0, s>>>(static_cast<const RepackDesc*>(B.d_rep), B.count);
   if (cudaGetLastError() != cudaSuccess) return ROT_ECUDA;
   auto kfn = wave_batched_kernel<double, kKMAX, kNBT, kWarps>;
-  const int tr = trace_begin(ROT_KERNEL_WAVE_BATCHED, P->rotation_rows, s);
-  kfn<<<(unsigned)P->grid, kWarps * 32, P->smem, s>>>(P->d_inst, P->d_seg, P->nseg, P->launch);
+  const int tr = trace_begin(ROT_KERNEL_WAVE_BATCHED, B.rotation_rows, s);
+  kfn<<<(unsigned)B.grid, kWarps * 32, B.smem, s>>>(B.d_inst, B.d_seg, B.nseg, B.launch);
   trace_end(tr, s);
   if (cudaGetLastError() != cudaSuccess) return ROT_ECUDA;
-  record_status_async(P->launch.status, s);
+  record_status_async(B.launch.status, s);
   if (cudaGetLastError() != cudaSuccess) return ROT_ECUDA;
   count_launches(3);
   return ROT_OK;
@@ -251,7 +214,7 @@ static rot_status execute_plan(BatchPlan* P, cudaStream_t s) {
 }  // namespace rs
 
 struct rot_batch_plan_s {
-  rs::BatchPlan p;
+  rs::BatchLaunch p;   // p.base is the plan's own workspace
 };
 
 extern "C" {
@@ -263,7 +226,7 @@ rot_status rot_batch_plan_create(int count, const rot_problem* problems, const r
   // Validate everything before touching the device.
   {
     rs::BatchLayout probe;
-    rot_status v = rs::layout_plan(count, problems, rot_tuning{0, 0, 0}, &probe);
+    rot_status v = rs::batch_layout(count, problems, rot_tuning{0, 0, 0}, &probe);
     if (v != ROT_OK) return v;
   }
   rot_tuning tu{};
@@ -271,26 +234,30 @@ rot_status rot_batch_plan_create(int count, const rot_problem* problems, const r
   else rs::tuning_lookup(count, problems, &tu);
   if (tu.K < 0 || tu.K > 16 || tu.NB < 0 || tu.NB > 4096 || tu.ctas_per_sm < 0) return ROT_EINVAL;
   rs::BatchLayout L;
-  rot_status st = rs::layout_plan(count, problems, tu, &L);
+  rot_status st = rs::batch_layout(count, problems, tu, &L);
   if (st != ROT_OK) return st;
   auto* h = new (std::nothrow) rot_batch_plan_s;
   if (!h) return ROT_ENOMEM;
   h->p.tuning = tu;
-  h->p.ws_bytes = L.total;
   if (cudaGetDevice(&h->p.device) != cudaSuccess) { delete h; return ROT_ECUDA; }
   if (!L.idx.empty()) {
-    if (cudaMalloc(&h->p.ws, h->p.ws_bytes) != cudaSuccess) { cudaGetLastError(); delete h; return ROT_ENOMEM; }
-    st = rs::upload_plan(L, problems, &h->p);
-    if (st == ROT_OK) st = rs::prepare_launch(&h->p);
-    if (st != ROT_OK) { cudaFree(h->p.ws); delete h; return st; }
+    void* ws = nullptr;
+    if (cudaMalloc(&ws, L.total) != cudaSuccess) { cudaGetLastError(); delete h; return ROT_ENOMEM; }
+    std::vector<unsigned char> img(L.o_cs);
+    st = rs::batch_image(L, problems, static_cast<unsigned char*>(ws), img.data(), &h->p);
+    if (st == ROT_OK && cudaMemcpy(ws, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      st = ROT_ECUDA;
+    if (st == ROT_OK) st = rs::batch_prepare(&h->p);
+    if (st != ROT_OK) { cudaFree(ws); delete h; return st; }
   }
+  h->p.bytes = L.total;
   *out = h;
   return ROT_OK;
 }
 
 rot_status rot_batch_plan_execute(rot_batch_plan* plan, void* stream) {
   if (!plan) return ROT_EINVAL;
-  return rs::execute_plan(&plan->p, static_cast<cudaStream_t>(stream));
+  return rs::batch_enqueue(plan->p, static_cast<cudaStream_t>(stream));
 }
 
 rot_status rot_batch_plan_info(const rot_batch_plan* plan, rot_batch_info* info) {
@@ -298,7 +265,7 @@ rot_status rot_batch_plan_info(const rot_batch_plan* plan, rot_batch_info* info)
   info->problems = plan->p.count;
   info->work_items = plan->p.total;
   info->rotation_rows = plan->p.rotation_rows;
-  info->workspace_bytes = plan->p.ws_bytes;
+  info->workspace_bytes = plan->p.bytes;
   info->tuning = plan->p.tuning;
   return ROT_OK;
 }
@@ -306,10 +273,10 @@ rot_status rot_batch_plan_info(const rot_batch_plan* plan, rot_batch_info* info)
 rot_status rot_batch_plan_destroy(rot_batch_plan* plan) {
   if (!plan) return ROT_OK;
   rot_status st = ROT_OK;
-  if (plan->p.ws) {
+  if (plan->p.base) {
     // The plan's workspace may still be in use by queued work.
     if (cudaDeviceSynchronize() != cudaSuccess) st = ROT_ECUDA;
-    if (cudaFree(plan->p.ws) != cudaSuccess) st = ROT_ECUDA;
+    if (cudaFree(plan->p.base) != cudaSuccess) st = ROT_ECUDA;
   }
   delete plan;
   return st;

@@ -1,0 +1,63 @@
+// rs_batch.h -- the pieces of a batched wavefront launch, shared by batch
+// plans (rs_batch.cu) and the serving scheduler (rs_server.cu).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "rs_internal.h"
+#include "rs_wave.cuh"
+
+namespace rs {
+
+// Host-side layout of one batched launch: which problems have work, their
+// tiling, the segment table and the offsets of every part of its workspace.
+struct BatchLayout {
+  std::vector<int> idx;               // problems with work
+  std::vector<WavePlan> wp;           // their tilings
+  std::vector<size_t> cs_off, done_off;
+  std::vector<WaveSegment> seg;
+  size_t done_ints = 0, cs_bytes = 0;
+  size_t o_inst = 0, o_tmap = 0, o_seg = 0, o_rep = 0, o_cnt = 0, o_cs = 0, total = 0;
+  size_t cnt_bytes = 0;
+  long long tickets = 0, rotation_rows = 0;
+};
+
+// Everything needed to enqueue one batched launch whose workspace is at `base`.
+struct BatchLaunch {
+  int device = 0;
+  int count = 0;                      // problems with work
+  rot_tuning tuning{};
+  unsigned char* base = nullptr;      // device workspace
+  size_t bytes = 0;
+  WaveInstance* d_inst = nullptr;
+  WaveSegment* d_seg = nullptr;
+  void* d_rep = nullptr;
+  unsigned char* d_counters = nullptr;
+  size_t counters_bytes = 0;
+  WaveLaunch launch{};
+  int nseg = 0;
+  long long total = 0;
+  int repack_grid_x = 1;
+  long long rotation_rows = 0;
+  int grid = 1;
+  int smem = 0;
+};
+
+// Validate the problems and lay out a launch (no device calls).
+rot_status batch_layout(int count, const rot_problem* probs, const rot_tuning& tu, BatchLayout* L);
+
+// Fill the host image (L.o_cs bytes: descriptors, TMA descriptors, segments)
+// of a launch whose workspace will live at device address `dev_base`, and the
+// launch record.  No device calls; the caller copies img to dev_base.
+rot_status batch_image(const BatchLayout& L, const rot_problem* probs, unsigned char* dev_base,
+                       unsigned char* img, BatchLaunch* B);
+
+// Launch geometry on the current device (occupancy; not during stream capture).
+rot_status batch_prepare(BatchLaunch* B);
+
+// Enqueue: clear counters, repack C/S, the persistent kernel, fold the status.
+rot_status batch_enqueue(const BatchLaunch& B, cudaStream_t s);
+
+}  // namespace rs

@@ -69,3 +69,19 @@ def test_batch_plan_rejects_invalid_problems(lib):
                                      ctypes.cast(ctypes.pointer(bad), ctypes.c_void_p),
                                      ctypes.byref(h)) == 1
     assert lib.rot_batch_plan_destroy(None) == 0
+
+
+def test_server_argument_checks_without_device(lib):
+    from paper_2412_01852_gb300 import _native as nat
+    h = ctypes.c_void_p()
+    cfg = nat.ServerConfig(1000, 4, 2, 4)          # budget below 1 MiB
+    assert lib.rot_server_create(ctypes.cast(ctypes.pointer(cfg), ctypes.c_void_p), ctypes.byref(h)) == 1
+    cfg = nat.ServerConfig(1 << 30, 0, 2, 4)       # no request slots
+    assert lib.rot_server_create(ctypes.cast(ctypes.pointer(cfg), ctypes.c_void_p), ctypes.byref(h)) == 1
+    cfg = nat.ServerConfig(1 << 30, 4, 65, 4)      # too many streams
+    assert lib.rot_server_create(ctypes.cast(ctypes.pointer(cfg), ctypes.c_void_p), ctypes.byref(h)) == 1
+    assert lib.rot_server_create(None, ctypes.byref(h)) == 1
+    t = ctypes.c_uint64()
+    assert lib.rot_server_submit(None, 0, 4, None, 1, None, 1, ctypes.byref(t)) == 1
+    assert lib.rot_server_wait(None, 1, 0) == 1
+    assert lib.rot_server_destroy(None) == 0
