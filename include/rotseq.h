@@ -67,6 +67,10 @@ int rot_version(void);
 /* Human-readable name of a status code (static string, never NULL). */
 const char* rot_status_string(rot_status s);
 
+/* Description of the last failure recorded on the calling host thread (for
+ * ROT_ECUDA: the CUDA call and its error), or "" (never NULL). */
+const char* rot_last_error(void);
+
 /*
  * Algorithm 2 in FP64, computed in the wave order of Algorithm 3
  * (Section 1.1) by the row-parallel wavefront kernel.  Bit-identical to the
@@ -127,6 +131,52 @@ rot_status rot_apply_host(int64_t m, int64_t n, int64_t k, double* A_host, int64
 rot_status rot_apply_noalloc(int64_t m, int64_t n, int64_t k, double* A, int64_t lda,
                              const double* C, int64_t ldc, const double* S, int64_t lds,
                              void* stream);
+
+/* ---- accumulated blocks applied by matrix products (rs_gemm, Section 8) -- */
+
+typedef enum {
+  ROT_GEMM_F64_DMMA = 0,    /* FP64 tensor MMA, FP64 accumulation */
+  ROT_GEMM_SPLIT_BF16 = 1,  /* A, Q split into BF16 hi+lo; hi*hi+hi*lo+lo*hi, FP32 accumulation */
+  ROT_GEMM_SPLIT_F16 = 2    /* FP16 hi + 2^-11*lo; hi*hi and hi*lo+lo*hi in two FP32 accumulators */
+} rot_gemm_mode;
+
+/* Number of accumulated blocks for (n, k, nb, kb): for each group of kb
+ * sequences (p-block), ceil(((n-2) + kb') / nb) blocks of nb waves, where
+ * kb' = min(kb, k - p0).  0 when n < 2 or k < 1. */
+int64_t rot_form_blocks_count(int64_t n, int64_t k, int nb, int kb);
+
+/*
+ * Form every accumulated block in FP64 (the paper's rs_gemm accumulates
+ * blocks of rotations into orthogonal matrices).  Block b covers sequences
+ * [p0, p0+kb) and waves w = j + (p - p0) in [w0, w0+nb) of that p-block; it
+ * touches the L = nb + kb columns starting at c0 = w0 - kb + 1.  Q receives
+ * rot_form_blocks_count() matrices of L x L, column-major, one after the
+ * other (Q + b*L*L): block b's rotations applied, in Algorithm 2 order, to
+ * the identity (columns outside [0, n) stay identity), so that
+ * A(:, c0:c0+L) * Q_b equals applying the block to A.  Blocks are ordered
+ * by p-block, then by w0.  Entries equal the same computation on the CPU with
+ * this library's FMA placement; only the sign of zero entries may differ
+ * (rotations on two zeros are skipped).  Requirements: nb, kb multiples of
+ * 16, nb + kb <= 512; C, S, Q device memory.  Asynchronous on `stream`.
+ */
+rot_status rot_form_blocks(int64_t n, int64_t k, const double* C, int64_t ldc, const double* S,
+                           int64_t lds, int nb, int kb, double* Q, void* stream);
+
+/*
+ * Algorithm 2's result computed the rs_gemm way: form the blocks
+ * (rot_form_blocks, FP64), then update A block by block in the blocks' order,
+ * A(:, c0:c0+L) <- A(:, c0:c0+L) * Q_b, with tensor-core matrix products of
+ * the given mode (32-row tiles of A, one CTA each, mma.sync).  A stays FP64
+ * in memory.  Accuracy against the FP64 result: DMMA within
+ * 16*(k+nb+kb)*2^-53 per row; the split modes lose precision in the
+ * products (FP16 split: per-row relative error below 8*k*2^-24; BF16 split:
+ * about 2^-16 per block product).  Same arguments as rot_apply plus nb, kb
+ * (multiples of 16, nb + kb <= 512) and the mode.  Scratch (the blocks and
+ * their split copies) comes from the stream-ordered allocator.
+ */
+rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
+                          int64_t ldc, const double* S, int64_t lds, int nb, int kb, rot_gemm_mode mode,
+                          void* stream);
 
 /* ---- batches of independent problems ------------------------------------ */
 
@@ -278,7 +328,9 @@ typedef struct {
 enum {
   ROT_KERNEL_WAVE_F64 = 1,
   ROT_KERNEL_WAVE_F32 = 2,
-  ROT_KERNEL_WAVE_BATCHED = 3
+  ROT_KERNEL_WAVE_BATCHED = 3,
+  ROT_KERNEL_FORM_BLOCKS = 4,
+  ROT_KERNEL_GEMM_APPLY = 5
 };
 
 /* Start recording a CUDA event pair around every main kernel the library

@@ -25,6 +25,7 @@ sz = ctypes.c_size_t
 SIGNATURES = {
     "rot_version": (ci, []),
     "rot_status_string": (ctypes.c_char_p, [ci]),
+    "rot_last_error": (ctypes.c_char_p, []),
     "rot_apply": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_f32": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_device_status": (ci, []),
@@ -40,6 +41,9 @@ SIGNATURES = {
     "rot_batch_plan_destroy": (ci, [vp]),
     "rot_apply_batched": (ci, [ci, vp, vp]),
     "rot_batch_autotune": (ci, [ci, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]),
+    "rot_form_blocks_count": (i64, [i64, i64, ci, ci]),
+    "rot_form_blocks": (ci, [i64, i64, vp, i64, vp, i64, ci, ci, vp, vp]),
+    "rot_apply_gemm": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, ci, ci, ci, vp]),
     "rot_server_create": (ci, [vp, ctypes.POINTER(vp)]),
     "rot_server_register": (ci, [vp, i64, i64, vp, i64, ctypes.POINTER(ci)]),
     "rot_server_submit": (ci, [vp, ci, i64, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_uint64)]),
@@ -84,13 +88,20 @@ class TraceRecord(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("ms", ctypes.c_float), ("work", ctypes.c_int64)]
 
 
-KERNEL_KINDS = {1: "wave_f64", 2: "wave_f32", 3: "wave_batched"}
+KERNEL_KINDS = {1: "wave_f64", 2: "wave_f32", 3: "wave_batched", 4: "form_blocks", 5: "gemm_apply"}
+GEMM_MODES = {"dmma": 0, "bf16": 1, "f16": 2}
 
 
 class RotError(RuntimeError):
     def __init__(self, code, where=""):
         self.code = int(code)
-        super().__init__("%s%s" % (where + ": " if where else "", status_string(code)))
+        detail = ""
+        try:
+            detail = load().rot_last_error().decode()
+        except Exception:
+            pass
+        super().__init__("%s%s%s" % (where + ": " if where else "", status_string(code),
+                                     " [" + detail + "]" if detail else ""))
 
 
 def lib_path() -> str:

@@ -300,3 +300,35 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---- accumulated blocks (rs_gemm) ----------------------------------------------------
+
+def form_blocks_count(n, k, nb, kb):
+    return int(_native.load().rot_form_blocks_count(int(n), int(k), int(nb), int(kb)))
+
+
+def rot_form_blocks(n, C, S, nb, kb, stream=None):
+    """All accumulated blocks (FP64): a (nblk, L, L) tensor whose [b] is Q_b transposed.
+
+    The library writes each L x L block column-major; viewed as a C-ordered
+    (L, L) array that is Q_b^T, so ``Q[b].T`` is Q_b.
+    """
+    lib = _native.load()
+    k = C.shape[1]
+    nblk = form_blocks_count(n, k, nb, kb)
+    L = nb + kb
+    Q = torch.empty((max(nblk, 1), L, L), dtype=torch.float64, device=C.device)
+    _native.check(lib.rot_form_blocks(int(n), int(k), _ptr(C), _ld(C, n - 1), _ptr(S), _ld(S, n - 1),
+                                      int(nb), int(kb), Q.data_ptr(), _stream_handle(stream)),
+                  "rot_form_blocks")
+    return Q[:nblk]
+
+
+def rot_apply_gemm(A, C, S, nb=256, kb=64, mode="f16", stream=None):
+    """Algorithm 2 via accumulated blocks and tensor-core products (mode: dmma, bf16, f16)."""
+    lib = _native.load()
+    m, n, k, pa, lda, pc, ldc, ps, lds = _args(A, C, S, torch.float64)
+    _native.check(lib.rot_apply_gemm(m, n, k, pa, lda, pc, ldc, ps, lds, int(nb), int(kb),
+                                     _native.GEMM_MODES[mode], _stream_handle(stream)), "rot_apply_gemm")
+    return A

@@ -177,18 +177,34 @@ rot_status batch_image(const BatchLayout& L, const rot_problem* probs, unsigned 
 rot_status batch_prepare(BatchLaunch* B) {
   auto kfn = wave_batched_kernel<double, kKMAX, kNBT, kWarps>;
   const int smem = kWarps * WaveSmem<double, kKMAX, kNBT>::kWarpBytes;
-  if (cudaGetDevice(&B->device) != cudaSuccess) return ROT_ECUDA;
-  if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-    return ROT_ECUDA;
+  cudaError_t e = cudaGetDevice(&B->device);
+  if (e != cudaSuccess) return cuda_failed(e, "batch_prepare: cudaGetDevice");
+  e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_failed(e, "batch_prepare: cudaFuncSetAttribute");
   int nsm = 0, occ = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B->device);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kWarps * 32, smem) != cudaSuccess || occ < 1)
-    return ROT_ECUDA;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kWarps * 32, smem);
+  if (e != cudaSuccess) return cuda_failed(e, "batch_prepare: occupancy");
+  if (occ < 1) return cuda_failed(cudaErrorInvalidConfiguration, "batch_prepare: occupancy 0");
   const int per_sm = B->tuning.ctas_per_sm > 0 ? std::min(B->tuning.ctas_per_sm, occ) : occ;
   long long grid = (long long)nsm * per_sm;
   grid = std::min<long long>(grid, (B->total + kWarps - 1) / kWarps);
   B->grid = (int)std::max<long long>(grid, 1);
   B->smem = smem;
+  return ROT_OK;
+}
+
+rot_status batch_launch_kernel(const BatchLaunch& B, cudaStream_t s, int trace_kind, long long work) {
+  auto kfn = wave_batched_kernel<double, kKMAX, kNBT, kWarps>;
+  const int tr = trace_begin(trace_kind, work, s);
+  kfn<<<(unsigned)B.grid, kWarps * 32, B.smem, s>>>(B.d_inst, B.d_seg, B.nseg, B.launch);
+  trace_end(tr, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_failed(e, "wave_batched_kernel launch");
+  record_status_async(B.launch.status, s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_failed(e, "status kernel launch");
+  count_launches(2);
   return ROT_OK;
 }
 
@@ -200,14 +216,9 @@ rot_status batch_enqueue(const BatchLaunch& B, cudaStream_t s) {
   dim3 rg(B.repack_grid_x, B.count);
   repack_batch_kernel<<<rg, 256, 0, s>>>(static_cast<const RepackDesc*>(B.d_rep), B.count);
   if (cudaGetLastError() != cudaSuccess) return ROT_ECUDA;
-  auto kfn = wave_batched_kernel<double, kKMAX, kNBT, kWarps>;
-  const int tr = trace_begin(ROT_KERNEL_WAVE_BATCHED, B.rotation_rows, s);
-  kfn<<<(unsigned)B.grid, kWarps * 32, B.smem, s>>>(B.d_inst, B.d_seg, B.nseg, B.launch);
-  trace_end(tr, s);
-  if (cudaGetLastError() != cudaSuccess) return ROT_ECUDA;
-  record_status_async(B.launch.status, s);
-  if (cudaGetLastError() != cudaSuccess) return ROT_ECUDA;
-  count_launches(3);
+  const rot_status st = batch_launch_kernel(B, s, ROT_KERNEL_WAVE_BATCHED, B.rotation_rows);
+  if (st != ROT_OK) return st;
+  count_launches(1);
   return ROT_OK;
 }
 

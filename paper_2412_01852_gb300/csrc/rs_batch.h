@@ -57,6 +57,10 @@ rot_status batch_image(const BatchLayout& L, const rot_problem* probs, unsigned 
 // Launch geometry on the current device (occupancy; not during stream capture).
 rot_status batch_prepare(BatchLaunch* B);
 
+// Launch the persistent batched kernel and the status fold for a prepared
+// launch (the only place the batched kernel is launched).
+rot_status batch_launch_kernel(const BatchLaunch& B, cudaStream_t s, int trace_kind, long long work);
+
 // Enqueue: clear counters, repack C/S, the persistent kernel, fold the status.
 rot_status batch_enqueue(const BatchLaunch& B, cudaStream_t s);
 

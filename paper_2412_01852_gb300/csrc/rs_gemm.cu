@@ -1,0 +1,578 @@
+// rs_gemm.cu -- the accumulated-block variant ("rs_gemm", Section 8):
+// the rotations of each parallelogram block (nb waves x kb sequences,
+// Section 2) are first accumulated in FP64 into an orthogonal
+// (nb+kb)-square matrix Q_b, and A is then updated block after block by the
+// matrix product A(:, window_b) <- A(:, window_b) * Q_b on tensor cores.
+//
+// Block formation: Q_b = the block's rotations applied to the identity, i.e.
+// Algorithm 4 on I.  Every block is one instance of the batched wavefront
+// kernel whose rotations are restricted to the block (a window of waves and a
+// range of j), so forming all blocks is one persistent FP64 launch.  Rows of
+// the identity start as unit vectors, which lets whole waves on zero columns
+// be skipped (values are unchanged; only the sign of zeros can differ).
+//
+// Block apply (mma.sync): one CTA per 32-row tile of A walks the blocks in
+// order.  Modes:
+//   ROT_GEMM_F64_DMMA   FP64 tensor MMA (m8n8k4), FP64 accumulation;
+//   ROT_GEMM_SPLIT_BF16 x = hi + lo in BF16; hi*hi + hi*lo + lo*hi in FP32;
+//   ROT_GEMM_SPLIT_F16  x = hi + lo*2^-11 in FP16; hi*hi in one FP32
+//                       accumulator, hi*lo + lo*hi in another, combined as
+//                       acc0 + 2^-11*acc1.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "rs_batch.h"
+
+namespace rs {
+namespace {
+
+constexpr int kKMAX = 16;
+constexpr int kNBT = 16;
+constexpr int kWarps = 8;
+constexpr int kTM = 32;        // rows of A per CTA in the apply kernel
+constexpr int kKC = 32;        // k rows of Q per staged chunk (split modes)
+constexpr int kKC64 = 16;      // k rows of Q per staged chunk (DMMA)
+constexpr int kLMax = 512;     // largest supported nb + kb
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+struct BlockPos {
+  int w0, p0;   // first wave (relative to its p-block) and first sequence
+};
+
+// Blocks in the order they are applied: p-blocks of kb sequences in order,
+// within one p-block the waves 0 .. (n-2)+(kb'-1) cut into runs of nb.
+std::vector<BlockPos> block_schedule(int64_t n, int64_t k, int nb, int kb) {
+  std::vector<BlockPos> out;
+  for (int64_t p0 = 0; p0 < k; p0 += kb) {
+    const int64_t kbe = std::min<int64_t>(kb, k - p0);
+    const int64_t nw = (n - 1) + (kbe - 1);
+    for (int64_t w0 = 0; w0 < nw; w0 += nb) out.push_back(BlockPos{(int)w0, (int)p0});
+  }
+  return out;
+}
+
+// Q holds nblk blocks of Lp x Lp (column-major); each becomes the L x L
+// identity padded with zeros.
+__global__ void identity_kernel(double* Q, int L, int Lp, long long nblk) {
+  const long long total = nblk * (long long)Lp * Lp;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long within = e % ((long long)Lp * Lp);
+    const int r = (int)(within % Lp), c = (int)(within / Lp);
+    Q[e] = (r == c && r < L) ? 1.0 : 0.0;
+  }
+}
+
+// Split Q into hi/lo halves of the mode's 16-bit type (same column-major layout).
+template <int MODE>
+__global__ void split_kernel(const double* __restrict__ Q, uint16_t* __restrict__ hi,
+                             uint16_t* __restrict__ lo, long long total) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double q = Q[e];
+    if (MODE == ROT_GEMM_SPLIT_BF16) {
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)q);
+      const __nv_bfloat16 l = __float2bfloat16_rn((float)(q - (double)__bfloat162float(h)));
+      hi[e] = __bfloat16_as_ushort(h);
+      lo[e] = __bfloat16_as_ushort(l);
+    } else {
+      const __half h = __float2half_rn((float)q);
+      const __half l = __float2half_rn((float)((q - (double)__half2float(h)) * 2048.0));
+      hi[e] = __half_as_ushort(h);
+      lo[e] = __half_as_ushort(l);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) {
+  return (uint32_t)a | ((uint32_t)b << 16);
+}
+
+template <int MODE>
+__device__ __forceinline__ void split_pair(double x0, double x1, uint32_t& h, uint32_t& l) {
+  if (MODE == ROT_GEMM_SPLIT_BF16) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn((float)x0), h1 = __float2bfloat16_rn((float)x1);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn((float)(x0 - (double)__bfloat162float(h0)));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn((float)(x1 - (double)__bfloat162float(h1)));
+    h = pack2(__bfloat16_as_ushort(h0), __bfloat16_as_ushort(h1));
+    l = pack2(__bfloat16_as_ushort(l0), __bfloat16_as_ushort(l1));
+  } else {
+    const __half h0 = __float2half_rn((float)x0), h1 = __float2half_rn((float)x1);
+    const __half l0 = __float2half_rn((float)((x0 - (double)__half2float(h0)) * 2048.0));
+    const __half l1 = __float2half_rn((float)((x1 - (double)__half2float(h1)) * 2048.0));
+    h = pack2(__half_as_ushort(h0), __half_as_ushort(h1));
+    l = pack2(__half_as_ushort(l0), __half_as_ushort(l1));
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
+  if (MODE == ROT_GEMM_SPLIT_BF16) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  } else {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  }
+}
+
+__device__ __forceinline__ void dmma884(double* d, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d[0]), "+d"(d[1])
+               : "d"(a), "d"(b));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+struct ApplyParams {
+  double* A;
+  int64_t lda;
+  int m, n;
+  int L;                    // nb + kb
+  int Lp;                   // L rounded up to a multiple of 32 (the tiling's width)
+  int nblk;
+  const int* c0;            // first window column of each block (may be negative)
+  const double* Q;          // nblk x Lp x Lp, column-major, zero beyond L (DMMA)
+  const uint16_t* Qhi;      // split modes
+  const uint16_t* Qlo;
+};
+
+// sA: the block's window of this CTA's 32 rows, FP64, column-major with a
+// 33-double column pitch.  Split modes stage Q in chunks of kKC k-rows as
+// [n][kKC + 8] halves (hi and lo); DMMA stages [n][kKC64 + 2] doubles.
+constexpr int kApitch = kTM + 1;
+
+template <int MODE, int NT>
+__global__ void __launch_bounds__(256, 1) apply_kernel(const ApplyParams P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  double* sA = reinterpret_cast<double*>(smem);
+  unsigned char* sQ = smem + (size_t)kLMax * kApitch * sizeof(double);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int group = lane >> 2, tig = lane & 3;
+  const int rh = warp & 1;            // rows [16 rh, 16 rh + 16)
+  const int cg = warp >> 1;           // cols [cg * L/4, (cg+1) * L/4)
+  const int L = P.L;
+  const int Lp = P.Lp;
+  const int r0 = blockIdx.x * kTM;
+  const int ncol0 = cg * (NT * 8);
+
+  for (int b = 0; b < P.nblk; ++b) {
+    const int c0 = P.c0[b];
+    // ---- stage the window of A (columns outside [0, n) and rows >= m read as 0)
+    {
+      const int row = tid & 31;
+      const int grow = r0 + row;
+      for (int col = tid >> 5; col < Lp; col += 8) {
+        const int gcol = c0 + col;
+        double v = 0.0;
+        if (col < L && grow < P.m && gcol >= 0 && gcol < P.n) v = P.A[(int64_t)gcol * P.lda + grow];
+        sA[col * kApitch + row] = v;
+      }
+    }
+    __syncthreads();
+
+    if (MODE == ROT_GEMM_F64_DMMA) {
+      double acc[2][NT][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int t = 0; t < NT; ++t) acc[mt][t][0] = acc[mt][t][1] = 0.0;
+      double* sQd = reinterpret_cast<double*>(sQ);
+      constexpr int QP = kKC64 + 2;     // k pitch (doubles) per n row
+      const double* Qb = P.Q + (int64_t)b * Lp * Lp;
+      for (int kc = 0; kc < Lp; kc += kKC64) {
+        // stage Q(kc .. kc+16, 0 .. Lp) as [n][k]
+        for (int e = tid; e < Lp * (kKC64 / 2); e += 256) {
+          const int nn = e / (kKC64 / 2), kk = (e % (kKC64 / 2)) * 2;
+          cp_async16(&sQd[nn * QP + kk], &Qb[(int64_t)nn * Lp + kc + kk]);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+#pragma unroll
+        for (int k4 = 0; k4 < kKC64; k4 += 4) {
+          double a[2];
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) a[mt] = sA[(kc + k4 + tig) * kApitch + rh * 16 + mt * 8 + group];
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            const double bq = sQd[(ncol0 + t * 8 + group) * QP + k4 + tig];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) dmma884(acc[mt][t], a[mt], bq);
+          }
+        }
+        __syncthreads();
+      }
+      // results back into sA (this CTA's rows of the window), then to A
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          const int rr = rh * 16 + mt * 8 + group;
+          const int cc = ncol0 + t * 8 + 2 * tig;
+          sA[cc * kApitch + rr] = acc[mt][t][0];
+          sA[(cc + 1) * kApitch + rr] = acc[mt][t][1];
+        }
+    } else {
+      float acc0[NT][4], acc1[NT][4];
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc0[t][i] = acc1[t][i] = 0.f;
+      uint16_t* sQh = reinterpret_cast<uint16_t*>(sQ);
+      constexpr int QP = kKC + 8;       // k pitch (halves) per n row
+      uint16_t* sQl = sQh + (size_t)kLMax * QP;
+      const uint16_t* Qh = P.Qhi + (int64_t)b * Lp * Lp;
+      const uint16_t* Ql = P.Qlo + (int64_t)b * Lp * Lp;
+      for (int kc = 0; kc < Lp; kc += kKC) {
+        for (int e = tid; e < Lp * (kKC / 8); e += 256) {
+          const int nn = e / (kKC / 8), kk = (e % (kKC / 8)) * 8;
+          cp_async16(&sQh[nn * QP + kk], &Qh[(int64_t)nn * Lp + kc + kk]);
+          cp_async16(&sQl[nn * QP + kk], &Ql[(int64_t)nn * Lp + kc + kk]);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kKC; ks += 16) {
+          // A fragment (16 x 16, row-major): rows rh*16 + group (+8), cols kc+ks+2tig (+1, +8, +9)
+          uint32_t ah[4], al[4];
+          const int ra = rh * 16 + group;
+          const int ka = kc + ks + 2 * tig;
+          split_pair<MODE>(sA[ka * kApitch + ra], sA[(ka + 1) * kApitch + ra], ah[0], al[0]);
+          split_pair<MODE>(sA[ka * kApitch + ra + 8], sA[(ka + 1) * kApitch + ra + 8], ah[1], al[1]);
+          split_pair<MODE>(sA[(ka + 8) * kApitch + ra], sA[(ka + 9) * kApitch + ra], ah[2], al[2]);
+          split_pair<MODE>(sA[(ka + 8) * kApitch + ra + 8], sA[(ka + 9) * kApitch + ra + 8], ah[3], al[3]);
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            const int nb_ = ncol0 + t * 8 + group;
+            uint32_t bh[2], bl[2];
+            bh[0] = *reinterpret_cast<const uint32_t*>(&sQh[nb_ * QP + ks + 2 * tig]);
+            bh[1] = *reinterpret_cast<const uint32_t*>(&sQh[nb_ * QP + ks + 8 + 2 * tig]);
+            bl[0] = *reinterpret_cast<const uint32_t*>(&sQl[nb_ * QP + ks + 2 * tig]);
+            bl[1] = *reinterpret_cast<const uint32_t*>(&sQl[nb_ * QP + ks + 8 + 2 * tig]);
+            mma16816<MODE>(acc0[t], ah, bh);
+            if (MODE == ROT_GEMM_SPLIT_BF16) {
+              mma16816<MODE>(acc0[t], ah, bl);
+              mma16816<MODE>(acc0[t], al, bh);
+            } else {
+              mma16816<MODE>(acc1[t], ah, bl);
+              mma16816<MODE>(acc1[t], al, bh);
+            }
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const int rr = rh * 16 + group;
+        const int cc = ncol0 + t * 8 + 2 * tig;
+        const double s1 = (MODE == ROT_GEMM_SPLIT_F16) ? (1.0 / 2048.0) : 0.0;
+        sA[cc * kApitch + rr] = (double)acc0[t][0] + s1 * (double)acc1[t][0];
+        sA[(cc + 1) * kApitch + rr] = (double)acc0[t][1] + s1 * (double)acc1[t][1];
+        sA[cc * kApitch + rr + 8] = (double)acc0[t][2] + s1 * (double)acc1[t][2];
+        sA[(cc + 1) * kApitch + rr + 8] = (double)acc0[t][3] + s1 * (double)acc1[t][3];
+      }
+    }
+    __syncthreads();
+    // ---- write the window back (coalesced over rows)
+    {
+      const int row = tid & 31;
+      const int grow = r0 + row;
+      for (int col = tid >> 5; col < L; col += 8) {
+        const int gcol = c0 + col;
+        if (grow < P.m && gcol >= 0 && gcol < P.n) P.A[(int64_t)gcol * P.lda + grow] = sA[col * kApitch + row];
+      }  // columns L .. Lp-1 are padding and are never stored
+    }
+    __syncthreads();
+  }
+}
+
+size_t apply_smem_bytes(int mode) {
+  const size_t a = (size_t)kLMax * kApitch * sizeof(double);
+  if (mode == ROT_GEMM_F64_DMMA) return a + (size_t)kLMax * (kKC64 + 2) * sizeof(double);
+  return a + 2 * (size_t)kLMax * (kKC + 8) * sizeof(uint16_t);
+}
+
+template <int MODE, int NT>
+cudaError_t launch_apply_nt(const ApplyParams& P, cudaStream_t s) {
+  const size_t smem = apply_smem_bytes(MODE);
+  cudaError_t e = cudaFuncSetAttribute(apply_kernel<MODE, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  apply_kernel<MODE, NT><<<(unsigned)ceil_div(P.m, kTM), 256, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_apply(const ApplyParams& P, cudaStream_t s) {
+  switch (P.Lp / 32) {
+    case 1: return launch_apply_nt<MODE, 1>(P, s);
+    case 2: return launch_apply_nt<MODE, 2>(P, s);
+    case 3: return launch_apply_nt<MODE, 3>(P, s);
+    case 4: return launch_apply_nt<MODE, 4>(P, s);
+    case 5: return launch_apply_nt<MODE, 5>(P, s);
+    case 6: return launch_apply_nt<MODE, 6>(P, s);
+    case 7: return launch_apply_nt<MODE, 7>(P, s);
+    case 8: return launch_apply_nt<MODE, 8>(P, s);
+    case 9: return launch_apply_nt<MODE, 9>(P, s);
+    case 10: return launch_apply_nt<MODE, 10>(P, s);
+    case 11: return launch_apply_nt<MODE, 11>(P, s);
+    case 12: return launch_apply_nt<MODE, 12>(P, s);
+    case 13: return launch_apply_nt<MODE, 13>(P, s);
+    case 14: return launch_apply_nt<MODE, 14>(P, s);
+    case 15: return launch_apply_nt<MODE, 15>(P, s);
+    case 16: return launch_apply_nt<MODE, 16>(P, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// ---- block formation: one batched wave launch over all blocks ---------------------
+struct FormLayout {
+  std::vector<BlockPos> blocks;
+  std::vector<WaveInstance> inst;
+  std::vector<WavePlan> wp;
+  std::vector<WaveSegment> seg;
+  size_t done_ints = 0;
+  long long tickets = 0;
+  // workspace offsets
+  size_t o_cs = 0, o_tmap = 0, o_inst = 0, o_seg = 0, o_cnt = 0, cnt_bytes = 0, o_c0 = 0, total = 0;
+  int64_t W2 = 0;
+  int cs_rows = 0;
+};
+
+static void form_layout(int64_t n, int64_t k, int nb, int kb, FormLayout* F) {
+  F->blocks = block_schedule(n, k, nb, kb);
+  const int L = nb + kb;
+  const WavePlan gpl = plan_wave(1, n, k, kKMAX, kNBT, 0, 0, 8);
+  F->W2 = 2 * (int64_t)gpl.kpad;
+  F->cs_rows = gpl.cs_rows;
+  int max_key = 0;
+  for (const BlockPos& bp : F->blocks) {
+    const int kbe = (int)std::min<int64_t>(kb, k - bp.p0);
+    const int c0 = bp.w0 - kb + 1;
+    WavePlan pl = plan_wave(L, L, kbe, kKMAX, kNBT, 0, 0, 8);
+    WaveInstance I{};
+    I.m = L; I.n = L; I.k = kbe; I.lda = L;
+    I.K = pl.K; I.NB = pl.NB; I.delta = pl.delta; I.nchains = pl.nchains; I.G = pl.G; I.B = pl.B;
+    I.cs_row0 = c0 + bp.p0;
+    I.p_base = bp.p0;
+    I.j_lo = std::max(0, -c0);
+    I.j_hi = (int)std::min<int64_t>(L - 2, n - 2 - c0);
+    I.W_lo = kb - 1;
+    I.W_hi = kb - 1 + nb;
+    I.unit_rows = 1;
+    F->inst.push_back(I);
+    F->wp.push_back(pl);
+    max_key = std::max(max_key, (pl.B - 1) + pl.delta * (pl.G - 1));
+  }
+  const int ni = (int)F->inst.size();
+  std::vector<size_t> done_off(ni);
+  for (int t = 0; t < ni; ++t) {
+    done_off[t] = F->done_ints;
+    F->done_ints += (size_t)F->wp[t].nchains * F->wp[t].G;
+  }
+  for (int kappa = 0; kappa <= max_key; ++kappa)
+    for (int t = 0; t < ni; ++t) {
+      const WavePlan& pl = F->wp[t];
+      int hi = kappa / pl.delta;
+      if (hi > pl.G - 1) hi = pl.G - 1;
+      int lo = kappa - (pl.B - 1);
+      lo = lo <= 0 ? 0 : (lo + pl.delta - 1) / pl.delta;
+      if (hi < lo) continue;
+      F->seg.push_back(WaveSegment{F->tickets, t, kappa});
+      F->tickets += (long long)(hi - lo + 1) * pl.nchains;
+    }
+  size_t off = 0;
+  auto take = [&](size_t bytes, size_t align) {
+    off = (size_t)round_up((int64_t)off, (int64_t)align);
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  F->o_tmap = take(sizeof(CUtensorMap), 128);
+  F->o_inst = take(sizeof(WaveInstance) * std::max(ni, 1), 256);
+  F->o_seg = take(sizeof(WaveSegment) * std::max<size_t>(F->seg.size(), 1), 256);
+  F->o_c0 = take(sizeof(int) * std::max(ni, 1), 256);
+  F->cnt_bytes = (size_t)round_up((int64_t)(F->done_ints * sizeof(int)), 256) + 256;
+  F->o_cnt = take(F->cnt_bytes, 256);
+  F->o_cs = take((size_t)F->cs_rows * F->W2 * sizeof(double), 1024);
+  F->total = off;
+  // done pointers are set once the base address is known
+  for (int t = 0; t < ni; ++t) F->inst[t].done = reinterpret_cast<int*>(done_off[t] * sizeof(int));
+}
+
+// Form every block's Q (FP64) into Q (nblk x L x L) using workspace `ws`.
+// Blocks are written Lq x Lq apart with leading dimension Lq (Lq >= L; the
+// padding beyond L is zero).
+static rot_status form_blocks_enqueue(int64_t n, int64_t k, const double* C, int64_t ldc, const double* S,
+                                      int64_t lds, int nb, int kb, const FormLayout& F, unsigned char* ws,
+                                      double* Q, int Lq, cudaStream_t s) {
+  const int L = nb + kb;
+  const int ni = (int)F.inst.size();
+  std::vector<unsigned char> img(F.o_cs, 0);
+  CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(img.data() + F.o_tmap);
+  double* cs = reinterpret_cast<double*>(ws + F.o_cs);
+  if (!encode_tile_map_2d(ht, cs, true, (uint64_t)F.W2, (uint64_t)F.cs_rows, (uint64_t)F.W2 * sizeof(double),
+                          2 * kKMAX, kNBT)) {
+    note_error("form_blocks: cuTensorMapEncodeTiled failed");
+    return ROT_ECUDA;
+  }
+  WaveInstance* hi = reinterpret_cast<WaveInstance*>(img.data() + F.o_inst);
+  int* hc0 = reinterpret_cast<int*>(img.data() + F.o_c0);
+  int* d_done = reinterpret_cast<int*>(ws + F.o_cnt);
+  for (int t = 0; t < ni; ++t) {
+    WaveInstance I = F.inst[t];
+    I.A = Q + (int64_t)t * Lq * Lq;
+    I.lda = Lq;
+    I.done = d_done + reinterpret_cast<size_t>(F.inst[t].done) / sizeof(int);
+    I.tmap = reinterpret_cast<const CUtensorMap*>(ws + F.o_tmap);
+    hi[t] = I;
+    hc0[t] = F.blocks[t].w0 - kb + 1;
+  }
+  std::memcpy(img.data() + F.o_seg, F.seg.data(), F.seg.size() * sizeof(WaveSegment));
+  // The image is uploaded synchronously (it is small); the rest is queued.
+  cudaError_t e = cudaMemcpyAsync(ws, img.data(), img.size(), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_failed(e, "form_blocks: upload");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_failed(e, "form_blocks: synchronize");
+  e = cudaMemsetAsync(ws + F.o_cnt, 0, F.cnt_bytes, s);
+  if (e != cudaSuccess) return cuda_failed(e, "form_blocks: memset");
+  dim3 rb(32, 8);
+  dim3 rg((unsigned)ceil_div(n - 1, 32), (unsigned)ceil_div(k, 8));
+  repack_cs_kernel<double><<<rg, rb, 0, s>>>(C, ldc, S, lds, (int)n, (int)k, cs, F.W2, 0);
+  identity_kernel<<<1024, 256, 0, s>>>(Q, L, Lq, (long long)ni);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_failed(e, "form_blocks: repack/identity launch");
+  BatchLaunch B;
+  B.count = ni;
+  B.d_inst = reinterpret_cast<WaveInstance*>(ws + F.o_inst);
+  B.d_seg = reinterpret_cast<WaveSegment*>(ws + F.o_seg);
+  B.launch.ticket = reinterpret_cast<unsigned long long*>(ws + F.o_cnt +
+                                                          round_up((int64_t)(F.done_ints * sizeof(int)), 256));
+  B.launch.status = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(B.launch.ticket) + 64);
+  B.launch.total = F.tickets;
+  B.nseg = (int)F.seg.size();
+  B.total = F.tickets;
+  rot_status st = batch_prepare(&B);
+  if (st != ROT_OK) return st;
+  st = batch_launch_kernel(B, s, ROT_KERNEL_FORM_BLOCKS, (long long)ni * L * nb * kb);
+  if (st != ROT_OK) return st;
+  count_launches(2);
+  return ROT_OK;
+}
+
+static rot_status validate_gemm(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* C,
+                                int64_t ldc, const void* S, int64_t lds, int nb, int kb, bool* quick) {
+  *quick = false;
+  if (m < 0 || n < 0 || k < 0) return ROT_EINVAL;
+  const int64_t lim = (int64_t(1) << 31) - 1;
+  if (m > lim || n > lim || k > lim || n + k > lim) return ROT_EINVAL;
+  if (nb < 16 || kb < 16 || nb % 16 || kb % 16 || nb + kb > kLMax) return ROT_EINVAL;
+  if (lda < std::max<int64_t>(1, m)) return ROT_EINVAL;
+  const int64_t nm1 = std::max<int64_t>(1, n - 1);
+  if (ldc < nm1 || lds < nm1) return ROT_EINVAL;
+  if (m == 0 || n <= 1 || k == 0) { *quick = true; return ROT_OK; }
+  if (!A || !C || !S) return ROT_EINVAL;
+  return ROT_OK;
+}
+
+}  // namespace rs
+
+extern "C" {
+
+int64_t rot_form_blocks_count(int64_t n, int64_t k, int nb, int kb) {
+  if (n < 2 || k < 1 || nb < 1 || kb < 1) return 0;
+  return (int64_t)rs::block_schedule(n, k, nb, kb).size();
+}
+
+rot_status rot_form_blocks(int64_t n, int64_t k, const double* C, int64_t ldc, const double* S, int64_t lds,
+                           int nb, int kb, double* Q, void* stream) {
+  bool quick;
+  const void* dummy = reinterpret_cast<const void*>(0x100);
+  rot_status v = rs::validate_gemm(1, n, k, dummy, 1, C, ldc, S, lds, nb, kb, &quick);
+  if (v != ROT_OK || quick) return v;
+  if (!Q) return ROT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rs::FormLayout F;
+  rs::form_layout(n, k, nb, kb, &F);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, F.total, s) != cudaSuccess) { cudaGetLastError(); return ROT_ENOMEM; }
+  rot_status st = rs::form_blocks_enqueue(n, k, C, ldc, S, lds, nb, kb, F, static_cast<unsigned char*>(ws), Q,
+                                          nb + kb, s);
+  cudaFreeAsync(ws, s);
+  return st;
+}
+
+rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
+                          int64_t ldc, const double* S, int64_t lds, int nb, int kb, rot_gemm_mode mode,
+                          void* stream) {
+  bool quick;
+  rot_status v = rs::validate_gemm(m, n, k, A, lda, C, ldc, S, lds, nb, kb, &quick);
+  if (v != ROT_OK || quick) return v;
+  if (mode != ROT_GEMM_F64_DMMA && mode != ROT_GEMM_SPLIT_BF16 && mode != ROT_GEMM_SPLIT_F16) return ROT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rs::FormLayout F;
+  rs::form_layout(n, k, nb, kb, &F);
+  const int L = nb + kb;
+  const int Lp = (int)rs::round_up(L, 32);
+  const int64_t nblk = (int64_t)F.blocks.size();
+  const size_t q_bytes = (size_t)nblk * Lp * Lp * sizeof(double);
+  const size_t split_bytes = mode == ROT_GEMM_F64_DMMA ? 0 : (size_t)nblk * Lp * Lp * sizeof(uint16_t);
+  const size_t o_q = rs::round_up((int64_t)F.total, 1024);
+  const size_t o_hi = rs::round_up((int64_t)(o_q + q_bytes), 1024);
+  const size_t o_lo = rs::round_up((int64_t)(o_hi + split_bytes), 1024);
+  const size_t total = o_lo + split_bytes + 1024;
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, total, s) != cudaSuccess) { cudaGetLastError(); return ROT_ENOMEM; }
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  double* Q = reinterpret_cast<double*>(base + o_q);
+  rot_status st = rs::form_blocks_enqueue(n, k, C, ldc, S, lds, nb, kb, F, base, Q, Lp, s);
+  if (st == ROT_OK) {
+    rs::ApplyParams P{};
+    P.A = A; P.lda = lda; P.m = (int)m; P.n = (int)n; P.L = L; P.Lp = Lp; P.nblk = (int)nblk;
+    P.c0 = reinterpret_cast<const int*>(base + F.o_c0);
+    P.Q = Q;
+    P.Qhi = reinterpret_cast<const uint16_t*>(base + o_hi);
+    P.Qlo = reinterpret_cast<const uint16_t*>(base + o_lo);
+    const long long qe = (long long)nblk * Lp * Lp;
+    cudaError_t e = cudaSuccess;
+    const int tr = rs::trace_begin(ROT_KERNEL_GEMM_APPLY, m * (n - 1) * k, s);
+    if (mode == ROT_GEMM_SPLIT_BF16) {
+      rs::split_kernel<ROT_GEMM_SPLIT_BF16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
+                                                                  const_cast<uint16_t*>(P.Qlo), qe);
+      e = rs::launch_apply<ROT_GEMM_SPLIT_BF16>(P, s);
+    } else if (mode == ROT_GEMM_SPLIT_F16) {
+      rs::split_kernel<ROT_GEMM_SPLIT_F16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
+                                                                 const_cast<uint16_t*>(P.Qlo), qe);
+      e = rs::launch_apply<ROT_GEMM_SPLIT_F16>(P, s);
+    } else {
+      e = rs::launch_apply<ROT_GEMM_F64_DMMA>(P, s);
+    }
+    rs::trace_end(tr, s);
+    rs::count_launches(mode == ROT_GEMM_F64_DMMA ? 1 : 2);
+    if (e != cudaSuccess) st = rs::cuda_failed(e, "rot_apply_gemm: apply kernel");
+  }
+  cudaFreeAsync(ws, s);
+  return st;
+}
+
+}  // extern "C"

@@ -30,6 +30,10 @@ bool encode_tile_map_2d(CUtensorMap* map, const void* base, bool is_double, uint
                         uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
                         uint32_t box_outer);
 
+// Record a failed CUDA call for rot_last_error(); returns ROT_ECUDA.
+rot_status cuda_failed(cudaError_t e, const char* where);
+void note_error(const char* what);
+
 // Launch counting and event tracing (rs_util.cu).
 void count_launches(int n);
 int trace_begin(int kind, long long work, cudaStream_t s);

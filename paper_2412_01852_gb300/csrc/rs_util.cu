@@ -3,6 +3,7 @@
 // denominator, and the host-buffer entry point.
 #include <atomic>
 #include <mutex>
+#include <cstdio>
 #include <vector>
 #include <cuda_runtime.h>
 #include "rs_internal.h"
@@ -10,6 +11,16 @@
 namespace rs {
 
 static std::atomic<long long> g_launches{0};
+
+static thread_local char g_last_error[256] = "";
+
+rot_status cuda_failed(cudaError_t e, const char* where) {
+  snprintf(g_last_error, sizeof g_last_error, "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+  cudaGetLastError();
+  return ROT_ECUDA;
+}
+
+void note_error(const char* what) { snprintf(g_last_error, sizeof g_last_error, "%s", what); }
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 struct TraceEntry {
@@ -59,6 +70,8 @@ __global__ void dfma_probe_kernel(double* out, double b, double c, int iters) {
 }  // namespace rs
 
 extern "C" {
+
+const char* rot_last_error(void) { return rs::g_last_error; }
 
 rot_status rot_trace_start(void) {
   std::lock_guard<std::mutex> lk(rs::g_trace_mu);

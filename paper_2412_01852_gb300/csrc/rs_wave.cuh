@@ -68,6 +68,7 @@ struct WaveInstance {
   int p_base;       // (c,s) tensor column pair of sequence p is p_base + p
   int j_lo, j_hi;   // rotations exist for j_lo <= j <= j_hi (normally 0, n-2)
   int W_lo, W_hi;   // and for j + p in [W_lo, W_hi) (normally everything)
+  int unit_rows;    // 1: row r of A starts as the unit vector e_r (accumulated blocks)
   int* done;        // [nchains * G] completed wave-blocks per (chain, p-block)
   const void* tmap; // TMA descriptor of the (c,s) tensor (global memory), batched kernel only
 };
@@ -79,6 +80,7 @@ __host__ __device__ inline void set_full_range(WaveInstance& I) {
   I.j_hi = I.n - 2;
   I.W_lo = 0;
   I.W_hi = 0x7fffffff;
+  I.unit_rows = 0;
 }
 
 // Kernel-wide state of one launch.
@@ -214,8 +216,15 @@ __device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap
 
   // Waves of this p-block that hold rotations: the full-sequence wave
   // j + p = w + p0 must lie in [W_lo, W_hi).
-  const int wr_lo = I.W_lo - p0;
+  int wr_lo = I.W_lo - p0;
   const int wr_hi = I.W_hi - p0;
+  // Rows that start as unit vectors e_r: before rotation (j, p) (p counted
+  // from the instance's first sequence) row r can be non-zero only in columns
+  // >= r - p - 1, because each sequence spreads a row's support at most one
+  // column to the left.  So for every row r >= 32c of this chain, rotation
+  // (j = w - l, p = p0 + l) acts on two zeros when w < 32c - p0 - 2, whatever
+  // l is: such waves are skipped.  Skipping changes at most the sign of zeros.
+  if (I.unit_rows) wr_lo = max(wr_lo, c * 32 - p0 - 2);
 
   // ---- stream (c,s) tiles and run the waves ---------------------------------
   const int ntiles = (w1 - w0 + NBT - 1) / NBT;

@@ -1,0 +1,115 @@
+"""Accumulated blocks (rs_gemm, Section 8) against the oracle.
+
+Block formation is FP64 and follows the same per-element operation order as
+the oracle's form_block, so every non-zero entry is bit-identical (zeros may
+differ in sign: rotations on two zeros are skipped).  The block apply uses
+tensor-core products; each mode is held to its stated error bound against the
+FP64 oracle, per row:
+  DMMA        16*(k+nb+kb)*2^-53
+  split FP16  8*k*2^-24
+  split BF16  4*ceil(k/kb)*2^-16   (two block products per element per p-block)
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_01852_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_01852_gb300 import api, build
+    build.build()
+    return api
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+
+
+def row_rel(out, ref):
+    return np.linalg.norm(out - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def bound(mode, k, nb, kb):
+    if mode == "dmma":
+        return 16 * (k + nb + kb) * U64
+    if mode == "f16":
+        return 8 * k * U32
+    return 4 * math.ceil(k / kb) * 2.0 ** -16
+
+
+@pytest.mark.parametrize("n,k,nb,kb", [(40, 9, 16, 16), (100, 40, 32, 16), (300, 64, 64, 32),
+                                       (70, 100, 48, 16), (600, 130, 256, 64)])
+def test_form_blocks_match_oracle(api, n, k, nb, kb):
+    C, S = wl.rotations(n, k, seed=n + k)
+    Q = api.rot_form_blocks(n, dev(C), dev(S), nb, kb)
+    torch.cuda.synchronize()
+    api.rot_device_status()
+    sched = oracle.block_schedule(n, k, nb, kb)
+    assert Q.shape[0] == len(sched) == api.form_blocks_count(n, k, nb, kb)
+    Qh = Q.cpu().numpy()
+    for b, (w0, p0) in enumerate(sched):
+        ref = oracle.form_block(C, S, n, w0, nb, p0, kb)
+        got = Qh[b].T
+        assert np.array_equal(got, ref), b                   # equal values (+0 == -0)
+        nz = ref != 0
+        assert np.array_equal(got[nz].view(np.uint64), ref[nz].view(np.uint64)), b
+
+
+@pytest.mark.parametrize("mode", ["dmma", "f16", "bf16"])
+@pytest.mark.parametrize("m,n,k,nb,kb", [(100, 300, 40, 64, 16), (33, 130, 70, 32, 32),
+                                         (257, 500, 64, 256, 64), (64, 40, 100, 16, 16)])
+def test_apply_gemm_within_bound(api, mode, m, n, k, nb, kb):
+    A, C, S = wl.problem(m, n, k, seed=m + n + k)
+    ref = oracle.rot_sequence(A, C, S)
+    Ad = dev(A)
+    api.rot_apply_gemm(Ad, dev(C), dev(S), nb=nb, kb=kb, mode=mode)
+    torch.cuda.synchronize()
+    api.rot_device_status()
+    out = Ad.cpu().numpy()
+    rel = row_rel(out, ref)
+    assert rel.max() <= bound(mode, k, nb, kb), rel.max()
+    if mode == "dmma":
+        viaq = oracle.rot_sequence_gemm(A, C, S, nb, kb)
+        assert np.max(np.abs(out - viaq)) <= 16 * (nb + kb) * U64 * np.abs(A).max() * 4
+
+
+@pytest.mark.parametrize("mode", ["dmma", "f16", "bf16"])
+def test_orthogonality_drift_on_identity(api, mode):
+    n, k, nb, kb = 256, 48, 64, 16
+    C, S = wl.rotations(n, k, seed=3)
+    Ad = dev(np.eye(n))
+    api.rot_apply_gemm(Ad, dev(C), dev(S), nb=nb, kb=kb, mode=mode)
+    torch.cuda.synchronize()
+    Q = Ad.cpu().numpy()
+    drift = np.abs(Q.T @ Q - np.eye(n)).max()
+    tol = {"dmma": 10 * n * U64, "f16": 8 * k * U32, "bf16": 8 * math.ceil(k / kb) * 2.0 ** -16}[mode]
+    assert drift <= tol, drift
+
+
+@pytest.mark.parametrize("mode", ["f16", "bf16", "dmma"])
+def test_precision_config_8192_sampled_rows(api, mode):
+    """A 8192 x 8192, k = 192, nb = 256, kb = 64: rows sampled against the FP64 oracle."""
+    cfg = wl.WORKLOADS["precision-8192"]
+    m, n, k, nb, kb = cfg["m"], cfg["n"], cfg["k"], cfg["nb"], cfg["kb"]
+    A, C, S = wl.problem(m, n, k, seed=cfg["seed"])
+    g = np.random.default_rng(8)
+    rows = np.unique(np.concatenate([[0, m - 1], g.choice(m, 10, replace=False)]))
+    ref = oracle.rot_sequence(A[rows], C, S)
+    Ad = dev(A)
+    api.rot_apply_gemm(Ad, dev(C), dev(S), nb=nb, kb=kb, mode=mode)
+    torch.cuda.synchronize()
+    api.rot_device_status()
+    out = Ad[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert row_rel(out, ref).max() <= bound(mode, k, nb, kb)
