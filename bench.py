@@ -221,12 +221,20 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-rows", type=int, default=512)
+    ap.add_argument("--variant", default="plain",
+                    choices=["plain", "f32", "gemm-f16", "gemm-bf16", "gemm-dmma", "batched", "serving"],
+                    help="plain (default) is the measured line; the others measure the other "
+                         "paths of the library on the same GPU")
+    ap.add_argument("--serve-requests", type=int, default=10000)
     args = ap.parse_args()
     cfg = dict(wl.WORKLOADS[args.workload])
     cfg["name"] = args.workload
 
     if args.impl == "reference":
         run_reference(args, cfg)
+        return
+    if args.variant != "plain":
+        run_variant(args)
         return
 
     import torch
@@ -344,6 +352,222 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------
+# Other paths of the library, measured on the same GPU (``--variant``).  Each prints one
+# JSON line with the same metric and unit as the plain line.
+# ---------------------------------------------------------------------------------------
+
+FP32_FMA_PER_SM_CLK = 128
+
+
+def _dev_colmajor(torch, a, dev, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a.T)).to(dev).t()
+    return t if dtype is None else t.to(dtype)
+
+
+def _row_rel(torch, out, ref):
+    d = torch.linalg.norm((out.double() - ref), dim=1)
+    return float((d / torch.linalg.norm(ref, dim=1)).max())
+
+
+def _timed_steps(torch, fn, steps, warmup, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_variant(args):
+    import torch
+    import paper_2412_01852_gb300 as rs
+    from paper_2412_01852_gb300 import api, build
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    clk = nominal_sm_clock_ghz(dev)
+    fp64_peak = props.multi_processor_count * FP64_FMA_PER_SM_CLK * 2 * clk / 1e3
+    fp32_peak = props.multi_processor_count * FP32_FMA_PER_SM_CLK * 2 * clk / 1e3
+    line = {"metric": METRIC, "unit": UNIT, "variant": args.variant, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic"}
+
+    if args.variant == "f32" or args.variant.startswith("gemm-"):
+        cfg = wl.WORKLOADS["precision-8192"]
+        m, n, k = cfg["m"], cfg["n"], cfg["k"]
+        A, C, S = wl.problem(m, n, k, cfg["seed"])
+        W = wl.rotation_rows(m, n, k)
+        A64 = _dev_colmajor(torch, A, dev)
+        C64 = _dev_colmajor(torch, C, dev)
+        S64 = _dev_colmajor(torch, S, dev)
+        ref = rs.colmajor(A64)
+        rs.rot_apply(ref, C64, S64)                     # the FP64 path's result, for the error
+        if args.variant == "f32":
+            A32, C32, S32 = rs.colmajor(A64.float()), rs.colmajor(C64.float()), rs.colmajor(S64.float())
+            once = rs.colmajor(A32)
+            rs.rot_apply_f32(once, C32, S32)
+            err = _row_rel(torch, once, ref)
+            fn = lambda: rs.rot_apply_f32(A32, C32, S32)
+            kind, peak, dtype = "wave_f32", fp32_peak, "f32"
+            cfg_line = {"workload": "precision-8192 FP32: A 8192x8192, C/S 8191x192 rounded to FP32", "m": m,
+                        "n": n, "k": k}
+        else:
+            mode = args.variant.split("-")[1]
+            nb, kb = cfg["nb"], cfg["kb"]
+            once = rs.colmajor(A64)
+            api.rot_apply_gemm(once, C64, S64, nb=nb, kb=kb, mode=mode)
+            err = _row_rel(torch, once, ref)
+            work = rs.colmajor(A64)
+            fn = lambda: api.rot_apply_gemm(work, C64, S64, nb=nb, kb=kb, mode=mode)
+            kind, peak, dtype = "form_blocks", fp64_peak, {"f16": "f16x2", "bf16": "bf16x2", "dmma": "f64"}[mode]
+            cfg_line = {"workload": "precision-8192 accumulated blocks: A 8192x8192, k=192, nb=%d, kb=%d, %s"
+                                    % (nb, kb, mode), "m": m, "n": n, "k": k, "nb": nb, "kb": kb, "mode": mode}
+        torch.cuda.synchronize()
+        rs.rot_device_status()
+        api.trace_start()
+        ms = _timed_steps(torch, fn, args.steps, args.warmup, stream)
+        recs = api.trace_stop()
+        rs.rot_device_status()
+        by = {}
+        for r in recs:
+            by.setdefault(r[0], []).append(r[1])
+        kernels = {kname: sum(v) / len(v) for kname, v in by.items()}
+        steps_traced = max(len(v) for v in by.values())
+        per_step = {kname: sum(v) / steps_traced for kname, v in by.items()}
+        line.update({"value": args.steps * W / (ms * 1e-3), "ms_per_step": ms / args.steps, "dtype": dtype,
+                     "config": cfg_line, "max_row_rel_err_vs_fp64_path": err, "kernel_ms_per_step": per_step})
+        if args.variant == "f32":
+            kms = kernels["wave_f32"]
+            line["roofline"] = {"bound": "alu", "achieved": 6.0 * W / (kms * 1e-3) / 1e12, "peak": peak,
+                                "unit": "TFLOP/s", "kernel": "wave_kernel<float>", "kernel_ms": kms,
+                                "peak_source": "nominal FP32 FMA rate: SMs x 128 x 2 x max SM clock"}
+            line["roofline"]["frac"] = line["roofline"]["achieved"] / peak
+        else:
+            kms = kernels.get("form_blocks", 0.0)
+            nblk = api.form_blocks_count(n, k, cfg["nb"], cfg["kb"])
+            form_rows = nblk * (cfg["nb"] + cfg["kb"]) * cfg["nb"] * cfg["kb"]
+            line["roofline"] = {"bound": "alu", "kernel": "wave_batched_kernel (block formation, FP64)",
+                                "achieved": 6.0 * form_rows / (kms * 1e-3) / 1e12, "peak": fp64_peak,
+                                "unit": "TFLOP/s", "kernel_ms": kms,
+                                "note": "achieved counts the rotations of all blocks on full identity rows "
+                                        "(zero waves are skipped, so this overstates executed flops)"}
+            line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
+        print(json.dumps(line), flush=True)
+        return
+
+    if args.variant == "batched":
+        shapes = wl.batch_shapes(512, seed=4)
+        probs = []
+        for i, (m, n, k) in enumerate(shapes):
+            A, C, S = wl.problem(m, n, k, seed=40000 + i)
+            probs.append((_dev_colmajor(torch, A, dev), _dev_colmajor(torch, C, dev), _dev_colmajor(torch, S, dev)))
+        W = sum(wl.rotation_rows(m, n, k) for (m, n, k) in shapes)
+        best, tune_ms = api.batch_autotune(probs)
+        plan = api.BatchPlan(probs)
+        s2 = torch.cuda.Stream()
+        with torch.cuda.stream(s2):
+            plan.execute()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s2):
+            plan.execute()
+        api.trace_start()
+        ms = _timed_steps(torch, g.replay, args.steps, args.warmup, stream)
+        recs = api.trace_stop()
+        rs.rot_device_status()
+        # the plain path on the same GPU, same instances one launch each, for comparison
+        def one_by_one():
+            for (Ad, Cd, Sd) in probs:
+                rs.rot_apply(Ad, Cd, Sd)
+        ms_single = _timed_steps(torch, one_by_one, 2, 1, stream)
+        line.update({"value": args.steps * W / (ms * 1e-3), "ms_per_step": ms / args.steps, "dtype": "f64",
+                     "config": {"workload": "batched: 512 instances, m log-uniform [64,4096], n log-uniform "
+                                            "[32,2048], k uniform [1,96], seed 4", "instances": 512,
+                                "rotation_rows_per_step": W, "tuning": best, "graph": True},
+                     "one_launch_per_instance": {"value": 2 * W / (ms_single * 1e-3), "ms_per_step": ms_single / 2},
+                     "roofline": {"bound": "alu", "kernel": "wave_batched_kernel", "peak": fp64_peak,
+                                  "unit": "TFLOP/s"}})
+        kms = [r[1] for r in recs if r[0] == "wave_batched"]
+        if kms:
+            line["roofline"]["kernel_ms"] = sum(kms) / len(kms)
+        else:  # launches replayed from a graph are not traced: use the step time
+            line["roofline"]["kernel_ms"] = ms / args.steps
+        line["roofline"]["achieved"] = 6.0 * W / (line["roofline"]["kernel_ms"] * 1e-3) / 1e12
+        line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
+        plan.close()
+        print(json.dumps(line), flush=True)
+        return
+
+    if args.variant == "serving":
+        sizes = wl.SERVING_SIZES
+        per_size = 4
+        mats, handles = [], {}
+        srv = api.Server(hbm_budget_bytes=4 << 30, max_inflight=256, streams=8, max_batch=64)
+        for s_i, nsz in enumerate(sizes):
+            for j in range(per_size):
+                Ad = _dev_colmajor(torch, wl.matrix(nsz, nsz, seed=7000 + 10 * s_i + j), dev)
+                mats.append(Ad)
+                handles.setdefault(nsz, []).append(srv.register(Ad))
+        pool = {nsz: [wl.rotations(nsz, 64, seed=8000 + 10 * s_i + j) for j in range(4)]
+                for s_i, nsz in enumerate(sizes)}
+        rng = np.random.default_rng(5)
+
+        def submit(req):
+            C, S = pool[req.n][int(rng.integers(0, 4))]
+            h = handles[req.n][int(rng.integers(0, per_size))]
+            return srv.submit(h, C[:, :req.k], S[:, :req.k]), wl.rotation_rows(req.n, req.n, req.k)
+
+        # capacity: a burst of requests, all submitted at once
+        burst = wl.serving_trace(min(args.serve_requests, 4000), 1e9, seed=5)
+        srv.stats(reset=True)
+        t0 = time.perf_counter()
+        tk = [submit(r)[0] for r in burst]
+        for t in tk:
+            srv.wait(t)
+        el = time.perf_counter() - t0
+        cap_rps = len(burst) / el
+        st_burst = srv.stats(reset=True)
+        levels = []
+        for frac in (0.25, 0.5, 0.9):
+            trace = wl.serving_trace(args.serve_requests, frac * cap_rps, seed=5 + int(frac * 100))
+            t0 = time.perf_counter()
+            tk = []
+            for r in trace:
+                d = t0 + r.arrival_s - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tk.append(submit(r)[0])
+            for t in tk:
+                srv.wait(t)
+            st = srv.stats(reset=True)
+            levels.append({"offered_load": frac, "offered_rps": frac * cap_rps, "requests": len(trace),
+                           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                           "throughput_rot_rows_per_s": st["rotation_rows_per_s"],
+                           "achieved_rps": st["completed"] / st["busy_s"] if st["busy_s"] > 0 else 0,
+                           "mean_batch": st["mean_batch"], "launches": st["launches"]})
+        srv.close()
+        rs.rot_device_status()
+        line.update({"value": st_burst["rotation_rows_per_s"], "dtype": "f64",
+                     "ms_per_step": None,
+                     "config": {"workload": "serving: Poisson arrivals, square A with n in {128..4096} "
+                                            "weights 1/n, k uniform [2,64], seed 5; %d resident matrices"
+                                            % len(mats), "requests_per_level": args.serve_requests,
+                                "server": {"hbm_budget_bytes": 4 << 30, "max_inflight": 256, "streams": 8,
+                                           "max_batch": 64}},
+                     "capacity": {"requests_per_s": cap_rps, "p50_ms": st_burst["p50_ms"],
+                                  "p99_ms": st_burst["p99_ms"], "mean_batch": st_burst["mean_batch"]},
+                     "loads": levels})
+        print(json.dumps(line), flush=True)
+        return
 
 
 if __name__ == "__main__":
