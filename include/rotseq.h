@@ -183,9 +183,14 @@ rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t ld
 /* Tiling of the wavefront kernel; 0 in a field means "default" (or the
  * autotuner's cached choice when a batch plan is created without tuning). */
 typedef struct {
-  int K;            /* sequences fused per work item, 1..16 (default 16) */
-  int NB;           /* waves per work item, rounded up to a multiple of 16 (default 64) */
-  int ctas_per_sm;  /* resident CTAs of 8 warps per SM (default: occupancy limit) */
+  int K;             /* sequences fused per work item, 1..16 (default 16) */
+  int NB;            /* waves per work item, rounded up to a multiple of 16 (default 32) */
+  int ctas_per_sm;   /* resident CTAs of 8 warps per SM (default: occupancy limit) */
+  int fp64_products; /* where the FP64 rotation's two products run: 0 default
+                        (= 1), 1 FP64 pipe (DMUL), 2 integer pipe (bit-identical
+                        emulation, DMUL only for zero, subnormal, Inf/NaN or
+                        out-of-range operands; slower on GB300); the FP32 path
+                        ignores it */
 } rot_tuning;
 
 /* One FP64 problem of a batch: A (m x n), C and S ((n-1) x k), all device
@@ -234,6 +239,11 @@ rot_status rot_batch_plan_info(const rot_batch_plan* plan, rot_batch_info* info)
 
 /* Free the plan (synchronizes the device first: queued work may use it). */
 rot_status rot_batch_plan_destroy(rot_batch_plan* plan);
+
+/* rot_apply with an explicit tiling (NULL or zero fields: defaults); the
+ * result is identical for every tiling.  ROT_EINVAL for out-of-range fields. */
+rot_status rot_apply_tuned(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
+                           int64_t ldc, const double* S, int64_t lds, const rot_tuning* tuning, void* stream);
 
 /* One-shot batch: create a plan, execute it on `stream`, wait, destroy. */
 rot_status rot_apply_batched(int count, const rot_problem* problems, void* stream);

@@ -40,6 +40,7 @@ SIGNATURES = {
     "rot_batch_plan_info": (ci, [vp, vp]),
     "rot_batch_plan_destroy": (ci, [vp]),
     "rot_apply_batched": (ci, [ci, vp, vp]),
+    "rot_apply_tuned": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp]),
     "rot_batch_autotune": (ci, [ci, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]),
     "rot_form_blocks_count": (i64, [i64, i64, ci, ci]),
     "rot_form_blocks": (ci, [i64, i64, vp, i64, vp, i64, ci, ci, vp, vp]),
@@ -68,7 +69,8 @@ class ServerStats(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("K", ctypes.c_int), ("NB", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+    _fields_ = [("K", ctypes.c_int), ("NB", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("fp64_products", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):

@@ -148,7 +148,7 @@ def _tuning(t):
     if t is None:
         return None
     if isinstance(t, dict):
-        t = (t.get("K", 0), t.get("NB", 0), t.get("ctas_per_sm", 0))
+        t = (t.get("K", 0), t.get("NB", 0), t.get("ctas_per_sm", 0), t.get("fp64_products", 0))
     return _native.Tuning(*t)
 
 
@@ -184,7 +184,8 @@ class BatchPlan:
                       "rot_batch_plan_info")
         return {"problems": inf.problems, "work_items": inf.work_items,
                 "rotation_rows": inf.rotation_rows, "workspace_bytes": inf.workspace_bytes,
-                "tuning": {"K": inf.tuning.K, "NB": inf.tuning.NB, "ctas_per_sm": inf.tuning.ctas_per_sm}}
+                "tuning": {"K": inf.tuning.K, "NB": inf.tuning.NB, "ctas_per_sm": inf.tuning.ctas_per_sm,
+                           "fp64_products": inf.tuning.fp64_products}}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -224,7 +225,8 @@ def batch_autotune(problems, stream=None):
                                          _stream_handle(stream),
                                          ctypes.cast(ctypes.pointer(best), ctypes.c_void_p),
                                          ctypes.byref(ms)), "rot_batch_autotune")
-    return {"K": best.K, "NB": best.NB, "ctas_per_sm": best.ctas_per_sm}, ms.value
+    return {"K": best.K, "NB": best.NB, "ctas_per_sm": best.ctas_per_sm,
+            "fp64_products": best.fp64_products}, ms.value
 
 
 # ---- serving -----------------------------------------------------------------------
@@ -331,4 +333,15 @@ def rot_apply_gemm(A, C, S, nb=256, kb=64, mode="f16", stream=None):
     m, n, k, pa, lda, pc, ldc, ps, lds = _args(A, C, S, torch.float64)
     _native.check(lib.rot_apply_gemm(m, n, k, pa, lda, pc, ldc, ps, lds, int(nb), int(kb),
                                      _native.GEMM_MODES[mode], _stream_handle(stream)), "rot_apply_gemm")
+    return A
+
+
+def rot_apply_tuned(A, C, S, tuning=None, stream=None):
+    """rot_apply with an explicit tiling dict {K, NB, ctas_per_sm} (same result for every tiling)."""
+    import ctypes
+    lib = _native.load()
+    t = _tuning(tuning)
+    _native.check(lib.rot_apply_tuned(*_args(A, C, S, torch.float64),
+                                      ctypes.cast(ctypes.pointer(t), ctypes.c_void_p) if t is not None else None,
+                                      _stream_handle(stream)), "rot_apply_tuned")
     return A

@@ -61,6 +61,24 @@ rot_status rot_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda,
                                static_cast<cudaStream_t>(stream), rs::WaveOptions{});
 }
 
+rot_status rot_apply_tuned(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
+                           int64_t ldc, const double* S, int64_t lds, const rot_tuning* tuning, void* stream) {
+  bool quick;
+  rot_status v = validate(m, n, k, A, lda, C, ldc, S, lds, &quick);
+  if (v != ROT_OK || quick) return v;
+  rs::WaveOptions o{};
+  if (tuning) {
+    if (tuning->K < 0 || tuning->K > 16 || tuning->NB < 0 || tuning->NB > 4096 || tuning->ctas_per_sm < 0 ||
+        tuning->fp64_products < 0 || tuning->fp64_products > 2)
+      return ROT_EINVAL;
+    o.K = tuning->K;
+    o.NB = tuning->NB;
+    o.ctas_per_sm = tuning->ctas_per_sm;
+    o.fp64_products = tuning->fp64_products;
+  }
+  return rs::wave_apply<double>(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream), o);
+}
+
 rot_status rot_device_status(void) {
   if (cudaDeviceSynchronize() != cudaSuccess) return ROT_ECUDA;
   const int s = rs::take_sticky_status();

@@ -174,8 +174,18 @@ rot_status batch_image(const BatchLayout& L, const rot_problem* probs, unsigned 
   return ROT_OK;
 }
 
+// The two instantiations of the batched kernel: FP64 products on the FP64
+// pipe or on the integer pipe (bit-identical results).
+static auto batched_fn(bool intmul) {
+  return intmul ? wave_batched_kernel<double, kKMAX, kNBT, kWarps, 2>
+                : wave_batched_kernel<double, kKMAX, kNBT, kWarps, 1>;
+}
+
 rot_status batch_prepare(BatchLaunch* B) {
-  auto kfn = wave_batched_kernel<double, kKMAX, kNBT, kWarps>;
+  const bool intmul = B->tuning.fp64_products == 2 ||
+                      (B->tuning.fp64_products == 0 && kDefaultFp64Products == 2);
+  B->intmul = intmul;
+  auto kfn = batched_fn(intmul);
   const int smem = kWarps * WaveSmem<double, kKMAX, kNBT>::kWarpBytes;
   cudaError_t e = cudaGetDevice(&B->device);
   if (e != cudaSuccess) return cuda_failed(e, "batch_prepare: cudaGetDevice");
@@ -195,7 +205,7 @@ rot_status batch_prepare(BatchLaunch* B) {
 }
 
 rot_status batch_launch_kernel(const BatchLaunch& B, cudaStream_t s, int trace_kind, long long work) {
-  auto kfn = wave_batched_kernel<double, kKMAX, kNBT, kWarps>;
+  auto kfn = batched_fn(B.intmul);
   const int tr = trace_begin(trace_kind, work, s);
   kfn<<<(unsigned)B.grid, kWarps * 32, B.smem, s>>>(B.d_inst, B.d_seg, B.nseg, B.launch);
   trace_end(tr, s);
@@ -243,7 +253,9 @@ rot_status rot_batch_plan_create(int count, const rot_problem* problems, const r
   rot_tuning tu{};
   if (tuning) tu = *tuning;
   else rs::tuning_lookup(count, problems, &tu);
-  if (tu.K < 0 || tu.K > 16 || tu.NB < 0 || tu.NB > 4096 || tu.ctas_per_sm < 0) return ROT_EINVAL;
+  if (tu.K < 0 || tu.K > 16 || tu.NB < 0 || tu.NB > 4096 || tu.ctas_per_sm < 0 || tu.fp64_products < 0 ||
+      tu.fp64_products > 2)
+    return ROT_EINVAL;
   rs::BatchLayout L;
   rot_status st = rs::batch_layout(count, problems, tu, &L);
   if (st != ROT_OK) return st;

@@ -43,6 +43,7 @@ struct BatchLaunch {
   long long rotation_rows = 0;
   int grid = 1;
   int smem = 0;
+  bool intmul = false;  // FP64 products on the integer pipe
 };
 
 // Validate the problems and lay out a launch (no device calls).

@@ -472,6 +472,7 @@ static rot_status form_blocks_enqueue(int64_t n, int64_t k, const double* C, int
   B.launch.total = F.tickets;
   B.nseg = (int)F.seg.size();
   B.total = F.tickets;
+  B.tuning.fp64_products = 1;  // identity rows are mostly zeros: keep the products on DMUL
   rot_status st = batch_prepare(&B);
   if (st != ROT_OK) return st;
   st = batch_launch_kernel(B, s, ROT_KERNEL_FORM_BLOCKS, (long long)ni * L * nb * kb);

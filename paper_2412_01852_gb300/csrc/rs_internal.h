@@ -9,10 +9,17 @@ namespace rs {
 
 // Per-call overrides of the wavefront kernel's tiling (0 = planner default).
 struct WaveOptions {
-  int K = 0;            // sequences per p-block (<= the kernel's window KMAX)
-  int NB = 0;           // waves per work item
-  int ctas_per_sm = 0;  // resident CTAs per SM (<= occupancy limit)
+  int K = 0;              // sequences per p-block (<= the kernel's window KMAX)
+  int NB = 0;             // waves per work item
+  int ctas_per_sm = 0;    // resident CTAs per SM (<= occupancy limit)
+  int fp64_products = 0;  // 0 default, 1 DMUL, 2 integer pipe
 };
+
+// The FP64 products used when a caller leaves the choice to the library.
+// Measured on GB300 (A 8192x8192, k = 192): DMUL 90.7 ms, integer pipe
+// 95.7 ms -- the FP64 pipe does not speed up when given fewer instructions
+// in this kernel, so the default stays on DMUL.
+constexpr int kDefaultFp64Products = 1;
 
 struct WavePlan {
   int K, NB, delta, nchains, G, B, kpad, cs_rows;

@@ -57,6 +57,7 @@ void load_file_locked() {
   if (!f) return;
   char key[160];
   rot_tuning t;
+  t.fp64_products = 0;
   while (std::fscanf(f, "%159s %d %d %d", key, &t.K, &t.NB, &t.ctas_per_sm) == 4) g_cache[key] = t;
   std::fclose(f);
 }
@@ -74,7 +75,7 @@ void store_locked(const std::string& key, const rot_tuning& t) {
 }  // namespace
 
 void tuning_lookup(int count, const rot_problem* problems, rot_tuning* out) {
-  *out = rot_tuning{0, 0, 0};
+  *out = rot_tuning{0, 0, 0, 0};
   if (count <= 0 || !problems) return;
   const std::string key = signature(count, problems);
   std::lock_guard<std::mutex> lk(g_mu);
@@ -107,7 +108,7 @@ extern "C" rot_status rot_batch_autotune(int count, const rot_problem* problems,
   const int NBs[] = {32, 64, 128};
   const int Cs[] = {1, 2};
   float best_t = -1.f;
-  rot_tuning bt{16, 64, 0};
+  rot_tuning bt{16, 32, 0, 0};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (st == ROT_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
     st = ROT_ECUDA;
@@ -115,7 +116,7 @@ extern "C" rot_status rot_batch_autotune(int count, const rot_problem* problems,
     for (int NB : NBs) {
       for (int C : Cs) {
         if (st != ROT_OK) break;
-        rot_tuning t{K, NB, C};
+        rot_tuning t{K, NB, C, 0};
         rot_batch_plan* plan = nullptr;
         st = rot_batch_plan_create(count, copy.data(), &t, &plan);
         if (st != ROT_OK) break;

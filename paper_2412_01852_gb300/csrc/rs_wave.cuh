@@ -26,6 +26,7 @@
 // completion on an mbarrier), and are read back with broadcast loads.
 #pragma once
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 #include <cuda.h>
 #include "rs_device.cuh"
@@ -50,6 +51,83 @@ __device__ __forceinline__ void rotate(float& x, float& y, float c, float s) {
   const float sx = __fmul_rn(s, x);
   const float xn = __fmaf_rn(c, x, sy);
   y = __fmaf_rn(c, y, -sx);
+  x = xn;
+}
+
+// RN(a*b) computed on the integer pipe, bit-identical to DMUL (IEEE round to
+// nearest even) whenever a and b are normal and the product is a normal
+// number that cannot overflow; `special` is set otherwise and the caller
+// must use DMUL.  GB300 issues FP64 at 2 lanes per clock per SM but integer
+// multiply-adds at 64, so moving the rotation's two products here leaves the
+// FP64 pipe only the two fused multiply-adds.
+//   a = Ma * 2^(ea-1075), b = Mb * 2^(eb-1075) with Ma, Mb in [2^52, 2^53).
+//   Ma*Mb = P in [2^104, 2^106); with ma = Ma<<11, mb = Mb<<11 the 128-bit
+//   product ma*mb = P*2^22, whose high word hi = floor(P/2^42) has its top
+//   bit t set iff P >= 2^105.  The rounded mantissa is hi >> (10+t) plus the
+//   round-to-even increment from the guard bit and the sticky bits (the rest
+//   of hi and the whole low word); the biased exponent is ea + eb - 1023 + t,
+//   and adding the 53-bit mantissa to (exponent-1)<<52 lets a rounding carry
+//   (mantissa 2^53) move into the exponent field exactly as IEEE requires.
+__host__ __device__ __forceinline__ unsigned long long umul64hi(unsigned long long a, unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+__host__ __device__ __forceinline__ unsigned long long bits_of(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long u;
+  memcpy(&u, &x, sizeof u);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ double double_of(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  memcpy(&x, &u, sizeof x);
+  return x;
+#endif
+}
+
+__host__ __device__ __forceinline__ double dmul_int(double a, double b, bool& special) {
+  const unsigned long long A = bits_of(a);
+  const unsigned long long B = bits_of(b);
+  const int ea = (int)(A >> 52) & 0x7ff;
+  const int eb = (int)(B >> 52) & 0x7ff;
+  const unsigned long long sign = (A ^ B) & 0x8000000000000000ull;
+  const unsigned long long ma = ((A & 0x000fffffffffffffull) | 0x0010000000000000ull) << 11;
+  const unsigned long long mb = ((B & 0x000fffffffffffffull) | 0x0010000000000000ull) << 11;
+  const unsigned long long hi = umul64hi(ma, mb);
+  const unsigned long long lo = ma * mb;
+  const unsigned t = (unsigned)(hi >> 63);
+  const unsigned sh = 10u + t;
+  unsigned long long mant = hi >> sh;
+  const unsigned long long guard = (hi >> (sh - 1u)) & 1ull;
+  const unsigned long long rest = (hi & ((1ull << (sh - 1u)) - 1ull)) | lo;
+  mant += guard & ((unsigned long long)(rest != 0ull) | (mant & 1ull));
+  const int e = ea + eb - 1023 + (int)t;
+  special = ((unsigned)(ea - 1) >= 2046u) | ((unsigned)(eb - 1) >= 2046u) | ((unsigned)(e - 1) >= 2045u);
+  return double_of(sign | ((((unsigned long long)(unsigned)(e - 1)) << 52) + mant));
+}
+
+// The FP64 rotation with both products on the integer pipe (same result as
+// rotate(double&, ...)); warps with any special lane recompute those
+// products with DMUL.
+__device__ __forceinline__ void rotate_intmul(double& x, double& y, double c, double s) {
+  bool sp1, sp2;
+  double sy = dmul_int(s, y, sp1);
+  double sx = dmul_int(s, x, sp2);
+  if (__any_sync(0xffffffffu, sp1 | sp2)) {
+    if (sp1) sy = __dmul_rn(s, y);
+    if (sp2) sx = __dmul_rn(s, x);
+  }
+  const double xn = __fma_rn(c, x, sy);
+  y = __fma_rn(c, y, -sx);
   x = xn;
 }
 
@@ -169,7 +247,9 @@ __device__ __forceinline__ WarpTiles<T, KMAX, NBT> warp_tiles_init(unsigned char
 
 // Work item (c, g, b) of instance I.  Returns false if the launch must stop
 // (an error was recorded in *status).
-template <typename T, int KMAX, int NBT>
+// INTMUL selects where the FP64 rotation's products run: 1 DMUL (rotate),
+// 2 on the integer pipe (rotate_intmul).  Both give bit-identical results.
+template <typename T, int KMAX, int NBT, int INTMUL>
 __device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap, int c, int g,
                                          int b, WarpTiles<T, KMAX, NBT>& wt, int lane,
                                          int* status) {
@@ -270,7 +350,8 @@ __device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap
         if (l > l_hi) break;
         if (l >= l_lo) {
           const V2 cs = trow[l];
-          rotate(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
+          if constexpr (INTMUL == 2 && sizeof(T) == 8) rotate_intmul(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
+          else rotate(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
         }
       }
       const int q = w + 1 - KMAX;            // column leaving the window
@@ -309,7 +390,7 @@ __device__ __forceinline__ long long next_ticket(unsigned long long* ticket, lon
 // Single instance: tickets decode in closed form (keys b + delta*g, within a
 // key p-block-major then chain-minor).  Every warp runs the ticket loop
 // independently; warps of a CTA share nothing but the CTA's shared memory.
-template <typename T, int KMAX, int NBT, int WARPS>
+template <typename T, int KMAX, int NBT, int WARPS, int INTMUL = 1>
 __global__ void __launch_bounds__(WARPS * 32)
 wave_kernel(const __grid_constant__ CUtensorMap tmap, const WaveProblem P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -341,14 +422,14 @@ wave_kernel(const __grid_constant__ CUtensorMap tmap, const WaveProblem P) {
     const int c = (int)(r - (long long)gi * P.nchains);
     const int g = kglo + gi;
     const int b = kappa - P.delta * g;
-    if (!run_item<T, KMAX, NBT>(P, &tmap, c, g, b, wt, lane, P.status)) break;
+    if (!run_item<T, KMAX, NBT, INTMUL>(P, &tmap, c, g, b, wt, lane, P.status)) break;
   }
 }
 
 // Many instances in one launch: tickets run through a host-built table of
 // segments (key, instance, first ticket), ordered by key and then instance,
 // so that every dependency of an item has a smaller ticket.
-template <typename T, int KMAX, int NBT, int WARPS>
+template <typename T, int KMAX, int NBT, int WARPS, int INTMUL = 1>
 __global__ void __launch_bounds__(WARPS * 32)
 wave_batched_kernel(const WaveInstance* __restrict__ insts, const WaveSegment* __restrict__ segs,
                     int nseg, const WaveLaunch L) {
@@ -373,7 +454,7 @@ wave_batched_kernel(const WaveInstance* __restrict__ insts, const WaveSegment* _
     const int c = (int)(r - (long long)gi * I.nchains);
     const int g = glo + gi;
     const int b = sg.key - I.delta * g;
-    if (!run_item<T, KMAX, NBT>(I, I.tmap, c, g, b, wt, lane, L.status)) break;
+    if (!run_item<T, KMAX, NBT, INTMUL>(I, I.tmap, c, g, b, wt, lane, L.status)) break;
   }
 }
 

@@ -75,7 +75,7 @@ WavePlan plan_wave(int64_t m, int64_t n, int64_t k, int kmax, int nbt, int K_req
   if (elem_bytes == 4 && pl.K < k && (pl.K & 1)) pl.K -= 1;
   if (pl.K < 1) pl.K = 1;
   if (elem_bytes == 4 && pl.K < k && (pl.K & 1)) pl.K = 2;
-  pl.NB = NB_req > 0 ? NB_req : 64;
+  pl.NB = NB_req > 0 ? NB_req : 32;
   if (pl.NB < nbt) pl.NB = nbt;
   pl.NB = (int)round_up(pl.NB, nbt);
   pl.delta = 1 + (int)ceil_div(pl.K, pl.NB);
@@ -89,11 +89,11 @@ WavePlan plan_wave(int64_t m, int64_t n, int64_t k, int kmax, int nbt, int K_req
 }
 
 // ---- launch -------------------------------------------------------------------
-template <typename T, int KMAX, int NBT, int WARPS>
+template <typename T, int KMAX, int NBT, int WARPS, int INTMUL>
 static cudaError_t launch_wave(const WaveProblem& P, const CUtensorMap& map, cudaStream_t stream,
                                int ctas_per_sm_req) {
   using SM = WaveSmem<T, KMAX, NBT>;
-  auto kfn = wave_kernel<T, KMAX, NBT, WARPS>;
+  auto kfn = wave_kernel<T, KMAX, NBT, WARPS, INTMUL>;
   const int smem = WARPS * SM::kWarpBytes;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
@@ -168,7 +168,15 @@ rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const 
     P.total = pl.total;
     const int tr = trace_begin(sizeof(T) == 8 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32,
                                (long long)m * (n - 1) * k, stream);
-    const cudaError_t le = launch_wave<T, KMAX, kNBT, kWarps>(P, map, stream, opt.ctas_per_sm);
+    const int prod = opt.fp64_products ? opt.fp64_products : kDefaultFp64Products;
+    cudaError_t le;
+    if constexpr (sizeof(T) == 8) {
+      if (prod == 2) le = launch_wave<T, KMAX, kNBT, kWarps, 2>(P, map, stream, opt.ctas_per_sm);
+      else le = launch_wave<T, KMAX, kNBT, kWarps, 1>(P, map, stream, opt.ctas_per_sm);
+    } else {
+      (void)prod;
+      le = launch_wave<T, KMAX, kNBT, kWarps, 1>(P, map, stream, opt.ctas_per_sm);
+    }
     trace_end(tr, stream);
     if (le != cudaSuccess) { st = ROT_ECUDA; break; }
     record_status_async(P.status, stream);

@@ -62,7 +62,7 @@ def test_batch_plan_rejects_invalid_problems(lib):
     assert lib.rot_batch_plan_create(3, ctypes.cast(arr, ctypes.c_void_p), None, ctypes.byref(h)) == 1
     assert lib.rot_batch_plan_create(-1, None, None, ctypes.byref(h)) == 1
     assert lib.rot_batch_plan_create(1, None, None, ctypes.byref(h)) == 1
-    bad = nat.Tuning(17, 64, 0)
+    bad = nat.Tuning(17, 64, 0, 0)
     arr2 = (nat.Problem * 1)()
     arr2[0] = nat.Problem(4, 4, 2, 0x1000, 4, 0x1000, 3, 0x1000, 3)
     assert lib.rot_batch_plan_create(1, ctypes.cast(arr2, ctypes.c_void_p),

@@ -139,6 +139,23 @@ def test_f32_bit_exact_and_error_bound(rs, m, n, k):
     assert rel.max() <= 8 * k * U32
 
 
+@pytest.mark.parametrize("products", [1, 2])
+@pytest.mark.parametrize("m,n,k", [(100, 77, 21), (257, 130, 17), (64, 300, 48), (33, 17, 5)])
+def test_f64_products_on_either_pipe_bit_exact(rs, m, n, k, products):
+    """FP64 products on DMUL (1) or on the integer pipe (2): the same bits as the oracle."""
+    from paper_2412_01852_gb300 import api
+    A, C, S = wl.problem(m, n, k, seed=m + 3 * n + 7 * k)
+    A[2 % m, 3] = 0.0          # zero entries take the DMUL fallback of the integer path
+    A[m - 1, 0] = 5e-310       # a subnormal entry as well
+    ref = oracle.rot_sequence(A, C, S)
+    Ad, _ = to_dev(A)
+    Cd, _ = to_dev(C)
+    Sd, _ = to_dev(S)
+    api.rot_apply_tuned(Ad, Cd, Sd, {"fp64_products": products})
+    rs.rot_device_status()
+    assert np.array_equal(bits(Ad.cpu().numpy()), bits(ref))
+
+
 def test_f64_paper_shaped_8192_sampled_rows(rs):
     """A 8192 x 8192, k = 192 (the measured workload), checked on sampled rows.
 
