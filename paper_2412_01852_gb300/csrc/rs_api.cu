@@ -57,8 +57,8 @@ rot_status rot_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda,
   bool quick;
   rot_status v = validate(m, n, k, A, lda, C, ldc, S, lds, &quick);
   if (v != ROT_OK || quick) return v;
-  return rs::wave_apply<float>(m, n, k, A, lda, C, ldc, S, lds,
-                               static_cast<cudaStream_t>(stream), rs::WaveOptions{});
+  return rs::wave_apply_f32(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream),
+                            rs::WaveOptions{});
 }
 
 rot_status rot_apply_tuned(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,

@@ -304,6 +304,136 @@ __global__ void __launch_bounds__(256, 1) apply_kernel(const ApplyParams P) {
   }
 }
 
+// Split modes, second design: the block's window of A is converted once into
+// hi/lo halves in shared memory ([row][k], pitch Lp+8 halves), Q_b arrives in
+// double-buffered chunks of 16 k-rows by cp.async ([n][k], pitch 24 halves),
+// and shared memory is sized for the block width so that two CTAs share an
+// SM and all 32-row tiles are resident at once.  Both pitches make the
+// fragment loads bank-conflict free: row g / tig t of a warp read banks
+// 4g + t (A, for Lp = 320) and 12g + t (Q) modulo 32.
+constexpr int kQP = 24;         // halves per n row of a staged Q chunk
+constexpr int kQK = 16;         // k rows per Q chunk
+
+template <int MODE, int NT>
+__global__ void __launch_bounds__(256, 2) apply_split_kernel(const ApplyParams P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int Lp = P.Lp, L = P.L;
+  const int AP = Lp + 8;                                   // A pitch (halves)
+  uint16_t* sAh = reinterpret_cast<uint16_t*>(smem);
+  uint16_t* sAl = sAh + kTM * AP;
+  uint16_t* sQ = sAl + kTM * AP;                           // [2 buffers][hi, lo][Lp][kQP]
+  const int qbuf = 2 * Lp * kQP;                           // halves per buffer (hi + lo)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int group = lane >> 2, tig = lane & 3;
+  const int rh = warp & 1, cg = warp >> 1;
+  const int r0 = blockIdx.x * kTM;
+  const int ncol0 = cg * (NT * 8);
+  const int nk = Lp / kQK;
+
+  for (int b = 0; b < P.nblk; ++b) {
+    const int c0 = P.c0[b];
+    const uint16_t* Qh = P.Qhi + (int64_t)b * Lp * Lp;
+    const uint16_t* Ql = P.Qlo + (int64_t)b * Lp * Lp;
+    auto stage_q = [&](int kc, int buf) {
+      uint16_t* dh = sQ + buf * qbuf;
+      uint16_t* dl = dh + Lp * kQP;
+      for (int e = tid; e < Lp * 2; e += 256) {            // two 16-byte pieces per n row
+        const int nn = e >> 1, kk = (e & 1) * 8;
+        cp_async16(&dh[nn * kQP + kk], &Qh[(int64_t)nn * Lp + kc + kk]);
+        cp_async16(&dl[nn * kQP + kk], &Ql[(int64_t)nn * Lp + kc + kk]);
+      }
+      cp_async_commit();
+    };
+    stage_q(0, 0);
+    // ---- the window of A, split into halves (8 loads in flight per thread)
+    {
+      const int row = tid & 31;
+      const int grow = r0 + row;
+      const bool rok = grow < P.m;
+      for (int col0 = tid >> 5; col0 < Lp; col0 += 64) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int col = col0 + 8 * u;
+          const int gcol = c0 + col;
+          v[u] = (col < L && rok && gcol >= 0 && gcol < P.n) ? P.A[(int64_t)gcol * P.lda + grow] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int col = col0 + 8 * u;
+          if (col < Lp) {
+            uint32_t h, l;
+            split_pair<MODE>(v[u], 0.0, h, l);
+            sAh[row * AP + col] = (uint16_t)(h & 0xffffu);
+            sAl[row * AP + col] = (uint16_t)(l & 0xffffu);
+          }
+        }
+      }
+    }
+    float acc0[NT][4], acc1[NT][4];
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc0[t][i] = acc1[t][i] = 0.f;
+    for (int kc = 0; kc < nk; ++kc) {
+      if (kc + 1 < nk) stage_q((kc + 1) * kQK, (kc + 1) & 1);
+      if (kc + 1 < nk) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      else cp_async_wait_all();
+      __syncthreads();
+      const uint16_t* qh = sQ + (kc & 1) * qbuf;
+      const uint16_t* ql = qh + Lp * kQP;
+      const int ka = kc * kQK + 2 * tig;
+      const int ra = rh * 16 + group;
+      uint32_t ah[4], al[4];
+      ah[0] = *reinterpret_cast<const uint32_t*>(&sAh[ra * AP + ka]);
+      ah[1] = *reinterpret_cast<const uint32_t*>(&sAh[(ra + 8) * AP + ka]);
+      ah[2] = *reinterpret_cast<const uint32_t*>(&sAh[ra * AP + ka + 8]);
+      ah[3] = *reinterpret_cast<const uint32_t*>(&sAh[(ra + 8) * AP + ka + 8]);
+      al[0] = *reinterpret_cast<const uint32_t*>(&sAl[ra * AP + ka]);
+      al[1] = *reinterpret_cast<const uint32_t*>(&sAl[(ra + 8) * AP + ka]);
+      al[2] = *reinterpret_cast<const uint32_t*>(&sAl[ra * AP + ka + 8]);
+      al[3] = *reinterpret_cast<const uint32_t*>(&sAl[(ra + 8) * AP + ka + 8]);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const int nb_ = ncol0 + t * 8 + group;
+        uint32_t bh[2], bl[2];
+        bh[0] = *reinterpret_cast<const uint32_t*>(&qh[nb_ * kQP + 2 * tig]);
+        bh[1] = *reinterpret_cast<const uint32_t*>(&qh[nb_ * kQP + 8 + 2 * tig]);
+        bl[0] = *reinterpret_cast<const uint32_t*>(&ql[nb_ * kQP + 2 * tig]);
+        bl[1] = *reinterpret_cast<const uint32_t*>(&ql[nb_ * kQP + 8 + 2 * tig]);
+        mma16816<MODE>(acc0[t], ah, bh);
+        if (MODE == ROT_GEMM_SPLIT_BF16) {
+          mma16816<MODE>(acc0[t], ah, bl);
+          mma16816<MODE>(acc0[t], al, bh);
+        } else {
+          mma16816<MODE>(acc1[t], ah, bl);
+          mma16816<MODE>(acc1[t], al, bh);
+        }
+      }
+      __syncthreads();   // the buffer read now is refilled two chunks later
+    }
+    // ---- results straight to A (columns past L are padding and are not stored)
+    const double s1 = (MODE == ROT_GEMM_SPLIT_F16) ? (1.0 / 2048.0) : 0.0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int cc = ncol0 + t * 8 + 2 * tig;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int rr = rh * 16 + group + (i >> 1) * 8;
+        const int col = cc + (i & 1);
+        const int grow = r0 + rr, gcol = c0 + col;
+        if (col < L && grow < P.m && gcol >= 0 && gcol < P.n)
+          P.A[(int64_t)gcol * P.lda + grow] = (double)acc0[t][i] + s1 * (double)acc1[t][i];
+      }
+    }
+    __syncthreads();   // the next block reads columns this block just wrote
+  }
+}
+
+size_t apply_split_smem_bytes(int Lp) {
+  return (size_t)2 * kTM * (Lp + 8) * sizeof(uint16_t) + (size_t)2 * 2 * Lp * kQP * sizeof(uint16_t);
+}
+
 size_t apply_smem_bytes(int mode) {
   const size_t a = (size_t)kLMax * kApitch * sizeof(double);
   if (mode == ROT_GEMM_F64_DMMA) return a + (size_t)kLMax * (kKC64 + 2) * sizeof(double);
@@ -312,12 +442,21 @@ size_t apply_smem_bytes(int mode) {
 
 template <int MODE, int NT>
 cudaError_t launch_apply_nt(const ApplyParams& P, cudaStream_t s) {
+  if constexpr (MODE != ROT_GEMM_F64_DMMA) {
+    const size_t smem = apply_split_smem_bytes(P.Lp);
+    cudaError_t e = cudaFuncSetAttribute(apply_split_kernel<MODE, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    apply_split_kernel<MODE, NT><<<(unsigned)ceil_div(P.m, kTM), 256, smem, s>>>(P);
+    return cudaGetLastError();
+  } else {
   const size_t smem = apply_smem_bytes(MODE);
   cudaError_t e = cudaFuncSetAttribute(apply_kernel<MODE, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   apply_kernel<MODE, NT><<<(unsigned)ceil_div(P.m, kTM), 256, smem, s>>>(P);
   return cudaGetLastError();
+  }
 }
 
 template <int MODE>

@@ -27,7 +27,10 @@ struct WavePlan {
 };
 
 WavePlan plan_wave(int64_t m, int64_t n, int64_t k, int kmax, int nbt, int K_req, int NB_req,
-                   int elem_bytes);
+                   int elem_bytes, int rows_per_chain = 32);
+
+rot_status wave_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C,
+                          int64_t ldc, const float* S, int64_t lds, cudaStream_t stream, const WaveOptions& opt);
 
 template <typename T>
 rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,

@@ -8,6 +8,7 @@
 #include <cudaTypedefs.h>
 
 #include "rs_wave.cuh"
+#include "rs_wave_f32.cuh"
 #include "rs_internal.h"
 
 namespace rs {
@@ -67,7 +68,7 @@ static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 static inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 WavePlan plan_wave(int64_t m, int64_t n, int64_t k, int kmax, int nbt, int K_req, int NB_req,
-                   int elem_bytes) {
+                   int elem_bytes, int rows_per_chain) {
   WavePlan pl{};
   pl.K = (int)std::min<int64_t>(K_req > 0 ? K_req : kmax, std::min<int64_t>(kmax, k));
   // The TMA x coordinate of p-block g is 2*g*K elements and must be a multiple
@@ -79,7 +80,7 @@ WavePlan plan_wave(int64_t m, int64_t n, int64_t k, int kmax, int nbt, int K_req
   if (pl.NB < nbt) pl.NB = nbt;
   pl.NB = (int)round_up(pl.NB, nbt);
   pl.delta = 1 + (int)ceil_div(pl.K, pl.NB);
-  pl.nchains = (int)ceil_div(m, 32);
+  pl.nchains = (int)ceil_div(m, rows_per_chain);
   pl.G = (int)ceil_div(k, pl.K);
   pl.B = (int)ceil_div(n + pl.K - 2, pl.NB);
   pl.total = (long long)pl.nchains * pl.G * pl.B;
@@ -126,7 +127,7 @@ template <typename T>
 rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
                       const T* S, int64_t lds, cudaStream_t stream, const WaveOptions& opt) {
   constexpr int KMAX = kmax_for<T>();
-  const WavePlan pl = plan_wave(m, n, k, KMAX, kNBT, opt.K, opt.NB, (int)sizeof(T));
+  const WavePlan pl = plan_wave(m, n, k, KMAX, kNBT, opt.K, opt.NB, (int)sizeof(T), 32);
 
   // Scratch: [repacked (c,s) | done counters | ticket | status]
   const int64_t W2 = 2 * (int64_t)pl.kpad;
@@ -187,11 +188,91 @@ rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const 
   return st;
 }
 
+// FP32: 64-row chains (2 rows per lane), 17-wave tiles, 4 tiles per item.
+static constexpr int kF32Kmax = 16;
+static constexpr int kF32R = 2;
+static constexpr int kF32NBT = kF32Kmax + 1;
+
+static cudaError_t launch_wave_f32(const WaveProblem& P, const CUtensorMap& map, cudaStream_t stream,
+                                   int ctas_per_sm_req) {
+  using SM = WaveSmem<float, kF32Kmax, kF32NBT>;
+  auto kfn = wave_f32_kernel<kF32Kmax, kF32R, kWarps>;
+  const int smem = kWarps * SM::kWarpBytes;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int per_sm = ctas_per_sm_req > 0 ? std::min(ctas_per_sm_req, occ) : occ;
+  long long want = std::min<long long>((long long)nsm * per_sm, (P.total + kWarps - 1) / kWarps);
+  kfn<<<(unsigned)std::max<long long>(want, 1), kWarps * 32, smem, stream>>>(map, P);
+  return cudaGetLastError();
+}
+
+rot_status wave_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C,
+                          int64_t ldc, const float* S, int64_t lds, cudaStream_t stream, const WaveOptions& opt) {
+  const WavePlan pl = plan_wave(m, n, k, kF32Kmax, kF32NBT, opt.K, opt.NB > 0 ? opt.NB : 4 * kF32NBT, 4,
+                                32 * kF32R);
+  const int64_t W2 = 2 * (int64_t)pl.kpad;
+  const size_t cs_bytes = (size_t)pl.cs_rows * W2 * sizeof(float);
+  const size_t done_off = round_up(cs_bytes, 256);
+  const size_t done_bytes = (size_t)pl.nchains * pl.G * sizeof(int);
+  const size_t tick_off = round_up(done_off + done_bytes, 256);
+  const size_t total_bytes = tick_off + 256;
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, total_bytes, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return ROT_ENOMEM;
+  }
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  rot_status st = ROT_OK;
+  do {
+    cudaError_t e = cudaMemsetAsync(base + done_off, 0, total_bytes - done_off, stream);
+    if (e != cudaSuccess) { st = cuda_failed(e, "rot_apply_f32: memset"); break; }
+    float* cs = reinterpret_cast<float*>(base);
+    dim3 rb(32, 8);
+    dim3 rg((unsigned)ceil_div(n - 1, 32), (unsigned)ceil_div(k, 8));
+    repack_cs_kernel<float><<<rg, rb, 0, stream>>>(C, ldc, S, lds, (int)n, (int)k, cs, W2, 0);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { st = cuda_failed(e, "rot_apply_f32: repack"); break; }
+    CUtensorMap map;
+    if (!encode_tile_map_2d(&map, cs, false, (uint64_t)W2, (uint64_t)pl.cs_rows, (uint64_t)W2 * sizeof(float),
+                            2 * kF32Kmax, kF32NBT)) {
+      note_error("rot_apply_f32: cuTensorMapEncodeTiled failed");
+      st = ROT_ECUDA;
+      break;
+    }
+    WaveProblem P{};
+    P.A = A; P.lda = lda; P.m = (int)m; P.n = (int)n; P.k = (int)k;
+    P.K = pl.K; P.NB = pl.NB; P.delta = pl.delta; P.nchains = pl.nchains; P.G = pl.G; P.B = pl.B;
+    P.cs_row0 = 0;
+    set_full_range(P);
+    P.done = reinterpret_cast<int*>(base + done_off);
+    P.ticket = reinterpret_cast<unsigned long long*>(base + tick_off);
+    P.status = reinterpret_cast<int*>(base + tick_off + 64);
+    P.total = pl.total;
+    const int tr = trace_begin(ROT_KERNEL_WAVE_F32, (long long)m * (n - 1) * k, stream);
+    e = launch_wave_f32(P, map, stream, opt.ctas_per_sm);
+    trace_end(tr, stream);
+    if (e != cudaSuccess) { st = cuda_failed(e, "rot_apply_f32: kernel launch"); break; }
+    record_status_async(P.status, stream);
+    count_launches(2);
+  } while (0);
+  cudaFreeAsync(scratch, stream);
+  return st;
+}
+
 template rot_status wave_apply<double>(int64_t, int64_t, int64_t, double*, int64_t, const double*,
                                        int64_t, const double*, int64_t, cudaStream_t,
                                        const WaveOptions&);
-template rot_status wave_apply<float>(int64_t, int64_t, int64_t, float*, int64_t, const float*,
-                                      int64_t, const float*, int64_t, cudaStream_t,
-                                      const WaveOptions&);
+
 
 }  // namespace rs
