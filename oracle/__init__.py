@@ -18,6 +18,8 @@ Functions and the passages they follow:
 * ``form_block``              -- the accumulated orthogonal block of rs_gemm (Section 8).
 * ``rot_sequence_gemm``       -- Algorithm 2 regrouped into accumulated blocks applied
                                  by FP64 matrix products (rs_gemm, Section 8).
+* ``refl_sequence``           -- 2x2 reflectors (tau, nu) in Algorithm 2's order (Section 6).
+* ``refl_sequence_reverse``   -- the same reflectors in reverse order (their inverse).
 
 Parity status: every function is pinned by ``tests/test_oracle_pins.py`` (closed
 forms, exact special cases, invariants, BLAS ``drot`` and exact rational
@@ -60,7 +62,7 @@ def _declare(lib):
     """Attach argument types to a loaded oracle library."""
     seq = [_i64, _i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
     for name in ("oracle_rot_sequence", "oracle_rot_sequence_wavefront",
-                 "oracle_rot_sequence_inverse"):
+                 "oracle_rot_sequence_inverse", "oracle_refl_sequence", "oracle_refl_sequence_reverse"):
         getattr(lib, name).argtypes = seq
         getattr(lib, name).restype = None
     lib.oracle_rot_sequence_f32.argtypes = [_i64, _i64, _i64, _fp, _i64, _fp, _i64, _fp, _i64]
@@ -145,6 +147,16 @@ def rot(x, y, c, s):
 def rot_sequence(A, C, S):
     """Algorithm 2: A * G(0,0) G(1,0) ... G(n-2,k-1), FP64."""
     return _run_seq("oracle_rot_sequence", A, C, S)
+
+
+def refl_sequence(A, T, V):
+    """2x2 reflectors H = I - tau*v*v^T, v = (1, nu), in Algorithm 2's order (Section 6)."""
+    return _run_seq("oracle_refl_sequence", A, T, V)
+
+
+def refl_sequence_reverse(A, T, V):
+    """The same reflectors applied in reverse order."""
+    return _run_seq("oracle_refl_sequence_reverse", A, T, V)
 
 
 def rot_sequence_wavefront(A, C, S):

@@ -175,3 +175,45 @@ void oracle_form_block(int64_t n, int64_t k,
         }
     }
 }
+
+/*
+ * 2x2 reflectors in place of rotations (Section 6): the reflector (tau, nu)
+ * is H = I - tau * v v^T with v = (1, nu)^T; applied to a row [x, y] it gives
+ *     x' = x - tau*(x + nu*y),   y' = y - nu*tau*(x + nu*y),
+ * three multiplications and three additions.  Placement of the fused
+ * operations (the paper fixes none; this is the reading used here):
+ *     t = fma(nu, y, x),  w = RN(tau*t),  x' = RN(x - w),  y' = fma(-nu, w, y).
+ * T(j,p) = T[j + p*ldt] holds tau, V(j,p) = V[j + p*ldv] holds nu; the
+ * reflectors are applied in Algorithm 2's order.
+ */
+static void refl_f64(int64_t m, double *x, double *y, double tau, double nu)
+{
+    for (int64_t i = 0; i < m; ++i) {
+        double xi = x[i], yi = y[i];
+        double t = fma(nu, yi, xi);
+        double w = tau * t;
+        x[i] = xi - w;
+        y[i] = fma(-nu, w, yi);
+    }
+}
+
+void oracle_refl_sequence(int64_t m, int64_t n, int64_t k,
+                          double *A, int64_t lda,
+                          const double *T, int64_t ldt,
+                          const double *V, int64_t ldv)
+{
+    for (int64_t p = 0; p < k; ++p)
+        for (int64_t j = 0; j + 1 < n; ++j)
+            refl_f64(m, A + j * lda, A + (j + 1) * lda, T[j + p * ldt], V[j + p * ldv]);
+}
+
+/* The same reflectors in reverse order (each 2x2 reflector is its own inverse). */
+void oracle_refl_sequence_reverse(int64_t m, int64_t n, int64_t k,
+                                  double *A, int64_t lda,
+                                  const double *T, int64_t ldt,
+                                  const double *V, int64_t ldv)
+{
+    for (int64_t p = k - 1; p >= 0; --p)
+        for (int64_t j = n - 2; j >= 0; --j)
+            refl_f64(m, A + j * lda, A + (j + 1) * lda, T[j + p * ldt], V[j + p * ldv]);
+}

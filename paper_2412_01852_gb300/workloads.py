@@ -57,6 +57,19 @@ def rotations(n: int, k: int, seed: int, dtype=np.float64):
     return C, S
 
 
+def reflectors(n: int, k: int, seed: int):
+    """(T, V) = (tau, nu) of 2x2 reflectors H = I - tau*v*v^T with v = (1, nu).
+
+    nu = tan(phi) with phi uniform in [-pi/4, pi/4] and tau = 2 / (1 + nu^2),
+    which makes every H orthogonal (up to the rounding of tau).
+    """
+    g = _rng(seed, 4)
+    phi = g.uniform(-math.pi / 4, math.pi / 4, size=(k, max(n - 1, 0)))
+    nu = np.tan(phi)
+    tau = 2.0 / (1.0 + nu * nu)
+    return np.asarray(tau.T, order="F"), np.asarray(nu.T, order="F")
+
+
 def problem(m: int, n: int, k: int, seed: int, dtype=np.float64):
     """(A, C, S) for one instance."""
     A = matrix(m, n, seed, dtype)

@@ -34,6 +34,10 @@ PINS = [
     lambda: pins.test_gemm_regrouping_equals_rotations(5, 70, 20, 16, 8),
     pins.test_f32_within_stated_error_of_f64,
     pins.test_f32_exact_special_case,
+    pins.test_reflector_closed_form_exact_rational_bound,
+    pins.test_reflector_is_an_involution_and_reverse_undoes_a_sequence,
+    pins.test_reflectors_orthogonal_and_norm_preserving,
+    pins.test_reflector_matches_matrix_definition,
 ]
 
 # (name, text to find, replacement, occurrence index among matches)
@@ -58,6 +62,9 @@ MUTANTS = [
     ("form_block_cs", "C[j + p * ldc], S[j + p * lds]);\n        }\n    }\n}",
      "S[j + p * lds], C[j + p * ldc]);\n        }\n    }\n}", 0),
     ("f32_sign", "y[i] = fmaf(c, yi, -sx);", "y[i] = fmaf(c, yi, sx);", 0),
+    ("refl_sign", "y[i] = fma(-nu, w, yi);", "y[i] = fma(nu, w, yi);", 0),
+    ("refl_dropped", "double t = fma(nu, yi, xi);", "double t = xi;", 0),
+    ("refl_tau", "double w = tau * t;", "double w = nu * t;", 0),
 ]
 
 

@@ -282,3 +282,53 @@ def test_degenerate_sizes_are_noops(m, n, k):
     S = np.zeros((max(n - 1, 0), k))
     out = oracle.rot_sequence(A, C, S)
     assert np.array_equal(out, A)
+
+
+# ------------------------------------------------------------ 2x2 reflectors
+def test_reflector_closed_form_exact_rational_bound():
+    """x' = x - tau(x + nu y), y' = y - nu tau (x + nu y), to within a few roundings."""
+    r = _rng(70)
+    for _ in range(200):
+        x, y = r.standard_normal(2)
+        nu = math.tan(r.uniform(-math.pi / 4, math.pi / 4))
+        tau = 2.0 / (1.0 + nu * nu)
+        out = oracle.refl_sequence(np.array([[x, y]]), np.array([[tau]]), np.array([[nu]]))
+        fx, fy, ft, fn = map(Fraction, (x, y, tau, nu))
+        t = fx + fn * fy
+        ex, ey = fx - ft * t, fy - fn * ft * t
+        b = Fraction(8 * U64 * (abs(x) + abs(y) + 1.0))
+        assert abs(Fraction(float(out[0, 0])) - ex) <= b
+        assert abs(Fraction(float(out[0, 1])) - ey) <= b
+
+
+def test_reflector_is_an_involution_and_reverse_undoes_a_sequence():
+    A = wl.matrix(10, 30, seed=71)
+    T, V = wl.reflectors(30, 9, seed=71)
+    one = oracle.refl_sequence(A, T[:, :1], V[:, :1])
+    # H H = I for one sequence applied twice in reverse order
+    back = oracle.refl_sequence_reverse(oracle.refl_sequence(A, T, V), T, V)
+    assert np.linalg.norm(back - A) <= 64 * 9 * 30 * U64 * np.linalg.norm(A)
+    assert not np.allclose(one, A)
+
+
+def test_reflectors_orthogonal_and_norm_preserving():
+    n, k = 40, 17
+    T, V = wl.reflectors(n, k, seed=72)
+    Q = oracle.refl_sequence(np.eye(n), T, V)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 16 * n * k * U64
+    # det = (-1)^(number of reflectors)
+    assert np.sign(np.linalg.det(Q)) == (-1) ** ((n - 1) * k)
+    A = wl.matrix(25, n, seed=73)
+    out = oracle.refl_sequence(A, T, V)
+    n0, n1 = np.linalg.norm(A, axis=1), np.linalg.norm(out, axis=1)
+    assert np.all(np.abs(n1 - n0) <= 16 * k * U64 * n0 * 4)
+
+
+def test_reflector_matches_matrix_definition():
+    """Each step equals multiplying by the 2x2 matrix I - tau v v^T (k = 1, n = 2, many rows)."""
+    A = wl.matrix(50, 2, seed=74)
+    T, V = wl.reflectors(2, 1, seed=74)
+    tau, nu = T[0, 0], V[0, 0]
+    H = np.eye(2) - tau * np.outer([1.0, nu], [1.0, nu])
+    out = oracle.refl_sequence(A, T, V)
+    assert np.max(np.abs(out - A @ H)) <= 16 * U64 * np.abs(A).max()
