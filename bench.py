@@ -222,7 +222,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-rows", type=int, default=512)
     ap.add_argument("--variant", default="plain",
-                    choices=["plain", "f32", "gemm-f16", "gemm-bf16", "gemm-dmma", "batched", "serving"],
+                    choices=["plain", "f32", "gemm-f16", "gemm-bf16", "gemm-dmma", "batched", "serving",
+                             "reflectors"],
                     help="plain (default) is the measured line; the others measure the other "
                          "paths of the library on the same GPU")
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -461,6 +462,30 @@ def run_variant(args):
                                 "note": "achieved counts the rotations of all blocks on full identity rows "
                                         "(zero waves are skipped, so this overstates executed flops)"}
             line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
+        print(json.dumps(line), flush=True)
+        return
+
+    if args.variant == "reflectors":
+        cfg = wl.WORKLOADS["plain-8192"]
+        m, n, k = cfg["m"], cfg["n"], cfg["k"]
+        A = wl.matrix(m, n, cfg["seed"])
+        T, V = wl.reflectors(n, k, cfg["seed"])
+        W = wl.rotation_rows(m, n, k)
+        Ad, Td, Vd = (_dev_colmajor(torch, X, dev) for X in (A, T, V))
+        api.trace_start()
+        ms = _timed_steps(torch, lambda: api.rot_apply_reflectors(Ad, Td, Vd), args.steps, args.warmup, stream)
+        recs = api.trace_stop()
+        rs.rot_device_status()
+        kms = [r[1] for r in recs if r[0] == "reflect_f64"]
+        kms = sum(kms) / len(kms)
+        line.update({"value": args.steps * W / (ms * 1e-3), "ms_per_step": ms / args.steps, "dtype": "f64",
+                     "config": {"workload": "reflectors: A 8192x8192 N(0,1), 2x2 reflectors (tau, nu) "
+                                            "8191x192, nu = tan(phi), phi uniform in [-pi/4, pi/4]",
+                                "m": m, "n": n, "k": k},
+                     "roofline": {"bound": "alu", "kernel": "wave_kernel<double, reflect>", "kernel_ms": kms,
+                                  "achieved": 6.0 * W / (kms * 1e-3) / 1e12, "peak": fp64_peak,
+                                  "unit": "TFLOP/s"}})
+        line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
         print(json.dumps(line), flush=True)
         return
 

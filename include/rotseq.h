@@ -94,6 +94,20 @@ rot_status rot_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda,
                          int64_t ldc, const float* S, int64_t lds, void* stream);
 
 /*
+ * 2x2 reflectors in place of rotations (Section 6): for p = 0..k-1 and
+ * j = 0..n-2 in Algorithm 2's order, columns j and j+1 of A are multiplied
+ * by the reflector H = I - tau*v*v^T with v = (1, nu), tau = T(j,p),
+ * nu = V(j,p):
+ *     x' = x - tau*(x + nu*y),   y' = y - nu*tau*(x + nu*y),
+ * computed as t = fma(nu, y, x), w = RN(tau*t), x' = RN(x - w),
+ * y' = fma(-nu, w, y) (bit-identical to a plain loop with that placement).
+ * Same kernel, arguments and error behaviour as rot_apply with (T, V) in
+ * place of (C, S); H is orthogonal when tau = 2/(1 + nu^2).
+ */
+rot_status rot_apply_reflectors(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* T,
+                               int64_t ldt, const double* V, int64_t ldv, void* stream);
+
+/*
  * Same computation as rot_apply on HOST buffers: copies A, C and S to the
  * current device, runs rot_apply on `stream`, copies A back into A_host and
  * synchronizes `stream` before returning.  Device memory comes from the
@@ -340,7 +354,8 @@ enum {
   ROT_KERNEL_WAVE_F32 = 2,
   ROT_KERNEL_WAVE_BATCHED = 3,
   ROT_KERNEL_FORM_BLOCKS = 4,
-  ROT_KERNEL_GEMM_APPLY = 5
+  ROT_KERNEL_GEMM_APPLY = 5,
+  ROT_KERNEL_REFLECT_F64 = 6
 };
 
 /* Start recording a CUDA event pair around every main kernel the library
@@ -359,6 +374,19 @@ int64_t rot_launch_count(void);
  * threads per SM): *gflops counts 2 flops per DFMA; *ms (optional) is the
  * time of one probe launch.  Synchronous. */
 rot_status rot_measure_fp64_peak(double* gflops, double* ms);
+
+/*
+ * Fault-detection self-test (the paper has no counterpart): runs the FP64
+ * wavefront kernel on a small scratch problem whose ticket counter starts
+ * past the first work item of every chain, so the items it hands out wait on
+ * dependency counters that nothing advances.  Each wait gives up after
+ * wait_ms (1..10000), records the timeout in the launch's status word and the
+ * kernel returns normally; nothing faults, traps or hangs, and the context
+ * stays usable.  Returns ROT_ETIMEOUT when the timeout was observed (the
+ * expected outcome), ROT_ECUDA otherwise.  Synchronous.  Does not touch the
+ * sticky status of rot_device_status.
+ */
+rot_status rot_selftest_wait_timeout(int wait_ms, void* stream);
 
 /*
  * Synchronizes the current device, then returns and clears the sticky

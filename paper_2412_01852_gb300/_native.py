@@ -29,7 +29,9 @@ SIGNATURES = {
     "rot_apply": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_f32": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_device_status": (ci, []),
+    "rot_selftest_wait_timeout": (ci, [ci, vp]),
     "rot_apply_host": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "rot_apply_reflectors": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_noalloc": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_trace_start": (ci, []),
     "rot_trace_stop": (ci, [vp, ci, ctypes.POINTER(ci)]),
@@ -90,7 +92,7 @@ class TraceRecord(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("ms", ctypes.c_float), ("work", ctypes.c_int64)]
 
 
-KERNEL_KINDS = {1: "wave_f64", 2: "wave_f32", 3: "wave_batched", 4: "form_blocks", 5: "gemm_apply"}
+KERNEL_KINDS = {1: "wave_f64", 2: "wave_f32", 3: "wave_batched", 4: "form_blocks", 5: "gemm_apply", 6: "reflect_f64"}
 GEMM_MODES = {"dmma": 0, "bf16": 1, "f16": 2}
 
 

@@ -345,3 +345,11 @@ def rot_apply_tuned(A, C, S, tuning=None, stream=None):
                                       ctypes.cast(ctypes.pointer(t), ctypes.c_void_p) if t is not None else None,
                                       _stream_handle(stream)), "rot_apply_tuned")
     return A
+
+
+def rot_apply_reflectors(A, T, V, stream=None):
+    """2x2 reflectors (tau = T, nu = V) in Algorithm 2's order, FP64, in place on A."""
+    lib = _native.load()
+    _native.check(lib.rot_apply_reflectors(*_args(A, T, V, torch.float64), _stream_handle(stream)),
+                  "rot_apply_reflectors")
+    return A

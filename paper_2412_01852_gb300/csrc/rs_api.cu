@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "rs_internal.h"
+#include "rs_device.cuh"
 
 namespace {
 
@@ -77,6 +78,24 @@ rot_status rot_apply_tuned(int64_t m, int64_t n, int64_t k, double* A, int64_t l
     o.fp64_products = tuning->fp64_products;
   }
   return rs::wave_apply<double>(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream), o);
+}
+
+rot_status rot_apply_reflectors(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* T,
+                               int64_t ldt, const double* V, int64_t ldv, void* stream) {
+  bool quick;
+  rot_status v = validate(m, n, k, A, lda, T, ldt, V, ldv, &quick);
+  if (v != ROT_OK || quick) return v;
+  rs::WaveOptions o{};
+  o.reflectors = true;
+  return rs::wave_apply<double>(m, n, k, A, lda, T, ldt, V, ldv, static_cast<cudaStream_t>(stream), o);
+}
+
+rot_status rot_selftest_wait_timeout(int wait_ms, void* stream) {
+  if (wait_ms < 1 || wait_ms > 10000) return ROT_EINVAL;
+  int dev_status = 0;
+  const rot_status st = rs::selftest_dependency_timeout(wait_ms, static_cast<cudaStream_t>(stream), &dev_status);
+  if (st != ROT_OK) return st;
+  return dev_status == rs::kDevTimeoutDependency ? ROT_ETIMEOUT : ROT_ECUDA;
 }
 
 rot_status rot_device_status(void) {

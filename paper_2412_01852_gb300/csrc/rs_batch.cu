@@ -177,8 +177,8 @@ rot_status batch_image(const BatchLayout& L, const rot_problem* probs, unsigned 
 // The two instantiations of the batched kernel: FP64 products on the FP64
 // pipe or on the integer pipe (bit-identical results).
 static auto batched_fn(bool intmul) {
-  return intmul ? wave_batched_kernel<double, kKMAX, kNBT, kWarps, 2>
-                : wave_batched_kernel<double, kKMAX, kNBT, kWarps, 1>;
+  return intmul ? wave_batched_kernel<double, kKMAX, kNBT, kWarps, kOpRotateIntmul>
+                : wave_batched_kernel<double, kKMAX, kNBT, kWarps, kOpRotate>;
 }
 
 rot_status batch_prepare(BatchLaunch* B) {

@@ -105,9 +105,11 @@ __device__ __forceinline__ void prefetch_tmap(const void* tmap) {
 }
 
 // ---- bounded spin on a progress counter -------------------------------------
-// Lane 0 waits until *flag >= need (acquire), giving up after kWaitLimitNs or
-// when *status becomes non-zero. Returns false if the wait did not succeed.
-__device__ __forceinline__ bool wait_flag_geq(const int* flag, int need, const int* status) {
+// Lane 0 waits until *flag >= need (acquire), giving up after limit_ns
+// (kWaitLimitNs unless a launch sets a shorter one) or when *status becomes
+// non-zero.  Returns false if the wait did not succeed.
+__device__ __forceinline__ bool wait_flag_geq(const int* flag, int need, const int* status,
+                                              unsigned long long limit_ns = kWaitLimitNs) {
   if (ld_acquire_gpu(flag) >= need) return true;
   const unsigned long long t0 = globaltimer_ns();
   unsigned ns = 32;
@@ -116,7 +118,7 @@ __device__ __forceinline__ bool wait_flag_geq(const int* flag, int need, const i
     if (ns < 1024) ns <<= 1;
     if (ld_acquire_gpu(flag) >= need) return true;
     if (ld_relaxed_gpu(status) != 0) return false;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
 

@@ -13,6 +13,7 @@ struct WaveOptions {
   int NB = 0;             // waves per work item
   int ctas_per_sm = 0;    // resident CTAs per SM (<= occupancy limit)
   int fp64_products = 0;  // 0 default, 1 DMUL, 2 integer pipe
+  bool reflectors = false; // the pairs are 2x2 reflectors (tau, nu) instead of (c, s)
 };
 
 // The FP64 products used when a caller leaves the choice to the library.
@@ -52,6 +53,8 @@ void trace_end(int id, cudaStream_t s);
 // Autotuner cache (rs_tune.cu): the tiling recorded for a batch of this shape,
 // or the defaults.
 void tuning_lookup(int count, const rot_problem* problems, rot_tuning* out);
+
+rot_status selftest_dependency_timeout(int wait_ms, cudaStream_t stream, int* device_status);
 
 // Sticky device status (first error recorded by any launch since the last read).
 int take_sticky_status();

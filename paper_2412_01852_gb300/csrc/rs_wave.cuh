@@ -131,6 +131,31 @@ __device__ __forceinline__ void rotate_intmul(double& x, double& y, double c, do
   x = xn;
 }
 
+// A 2x2 reflector H = I - tau*v*v^T, v = (1, nu), applied to the row pair
+// (Section 6: three multiplications and three additions), with the fixed
+// placement t = fma(nu, y, x), w = RN(tau*t), x' = RN(x - w), y' = fma(-nu, w, y).
+__device__ __forceinline__ void reflect(double& x, double& y, double tau, double nu) {
+  const double t = __fma_rn(nu, y, x);
+  const double w = __dmul_rn(tau, t);
+  const double xn = __dsub_rn(x, w);
+  y = __fma_rn(-nu, w, y);
+  x = xn;
+}
+__device__ __forceinline__ void reflect(float& x, float& y, float tau, float nu) {
+  const float t = __fmaf_rn(nu, y, x);
+  const float w = __fmul_rn(tau, t);
+  const float xn = __fsub_rn(x, w);
+  y = __fmaf_rn(-nu, w, y);
+  x = xn;
+}
+
+// What a wave kernel applies to each row pair.
+enum WaveOp : int {
+  kOpRotate = 1,        // rotation (c, s), products with DMUL
+  kOpRotateIntmul = 2,  // rotation (c, s), products on the integer pipe
+  kOpReflect = 3,       // 2x2 reflector (tau, nu)
+};
+
 // One instance of the problem as the wave kernel sees it.
 struct WaveInstance {
   void* A;          // column-major m x n, leading dimension lda (elements)
@@ -149,6 +174,7 @@ struct WaveInstance {
   int unit_rows;    // 1: row r of A starts as the unit vector e_r (accumulated blocks)
   int* done;        // [nchains * G] completed wave-blocks per (chain, p-block)
   const void* tmap; // TMA descriptor of the (c,s) tensor (global memory), batched kernel only
+  unsigned long long wait_ns;  // limit of one dependency wait (0: kWaitLimitNs)
 };
 
 // The whole problem: every rotation (j, p) with 0 <= j <= n-2, 0 <= p < k.
@@ -247,9 +273,9 @@ __device__ __forceinline__ WarpTiles<T, KMAX, NBT> warp_tiles_init(unsigned char
 
 // Work item (c, g, b) of instance I.  Returns false if the launch must stop
 // (an error was recorded in *status).
-// INTMUL selects where the FP64 rotation's products run: 1 DMUL (rotate),
-// 2 on the integer pipe (rotate_intmul).  Both give bit-identical results.
-template <typename T, int KMAX, int NBT, int INTMUL>
+// OP (a WaveOp) selects the operation on each row pair: a rotation with its
+// products on DMUL or on the integer pipe (bit-identical), or a reflector.
+template <typename T, int KMAX, int NBT, int OP>
 __device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap, int c, int g,
                                          int b, WarpTiles<T, KMAX, NBT>& wt, int lane,
                                          int* status) {
@@ -267,13 +293,14 @@ __device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap
   // ---- wait for dependencies ------------------------------------------------
   bool ok = true;
   if (lane == 0) {
-    if (b > 0) ok = wait_flag_geq(done + g, b, status);
+    const unsigned long long lim = I.wait_ns ? I.wait_ns : kWaitLimitNs;
+    if (b > 0) ok = wait_flag_geq(done + g, b, status, lim);
     if (ok && g > 0) {
       const int krp = I.K;                   // every p-block but the last is full
       const int Bp = (n + krp - 2 + I.NB - 1) / I.NB;
       int need = (w1 + krp + I.NB - 1) / I.NB;
       if (need > Bp) need = Bp;
-      ok = wait_flag_geq(done + g - 1, need, status);
+      ok = wait_flag_geq(done + g - 1, need, status, lim);
     }
     if (!ok) set_error(status, kDevTimeoutDependency);
   }
@@ -350,8 +377,12 @@ __device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap
         if (l > l_hi) break;
         if (l >= l_lo) {
           const V2 cs = trow[l];
-          if constexpr (INTMUL == 2 && sizeof(T) == 8) rotate_intmul(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
-          else rotate(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
+          if constexpr (OP == kOpRotateIntmul && sizeof(T) == 8)
+            rotate_intmul(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
+          else if constexpr (OP == kOpReflect)
+            reflect(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
+          else
+            rotate(win[KMAX - 1 - l], win[KMAX - l], cs.x, cs.y);
         }
       }
       const int q = w + 1 - KMAX;            // column leaving the window
@@ -390,7 +421,7 @@ __device__ __forceinline__ long long next_ticket(unsigned long long* ticket, lon
 // Single instance: tickets decode in closed form (keys b + delta*g, within a
 // key p-block-major then chain-minor).  Every warp runs the ticket loop
 // independently; warps of a CTA share nothing but the CTA's shared memory.
-template <typename T, int KMAX, int NBT, int WARPS, int INTMUL = 1>
+template <typename T, int KMAX, int NBT, int WARPS, int OP = kOpRotate>
 __global__ void __launch_bounds__(WARPS * 32)
 wave_kernel(const __grid_constant__ CUtensorMap tmap, const WaveProblem P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -422,14 +453,14 @@ wave_kernel(const __grid_constant__ CUtensorMap tmap, const WaveProblem P) {
     const int c = (int)(r - (long long)gi * P.nchains);
     const int g = kglo + gi;
     const int b = kappa - P.delta * g;
-    if (!run_item<T, KMAX, NBT, INTMUL>(P, &tmap, c, g, b, wt, lane, P.status)) break;
+    if (!run_item<T, KMAX, NBT, OP>(P, &tmap, c, g, b, wt, lane, P.status)) break;
   }
 }
 
 // Many instances in one launch: tickets run through a host-built table of
 // segments (key, instance, first ticket), ordered by key and then instance,
 // so that every dependency of an item has a smaller ticket.
-template <typename T, int KMAX, int NBT, int WARPS, int INTMUL = 1>
+template <typename T, int KMAX, int NBT, int WARPS, int OP = kOpRotate>
 __global__ void __launch_bounds__(WARPS * 32)
 wave_batched_kernel(const WaveInstance* __restrict__ insts, const WaveSegment* __restrict__ segs,
                     int nseg, const WaveLaunch L) {
@@ -454,7 +485,7 @@ wave_batched_kernel(const WaveInstance* __restrict__ insts, const WaveSegment* _
     const int c = (int)(r - (long long)gi * I.nchains);
     const int g = glo + gi;
     const int b = sg.key - I.delta * g;
-    if (!run_item<T, KMAX, NBT, INTMUL>(I, I.tmap, c, g, b, wt, lane, L.status)) break;
+    if (!run_item<T, KMAX, NBT, OP>(I, I.tmap, c, g, b, wt, lane, L.status)) break;
   }
 }
 

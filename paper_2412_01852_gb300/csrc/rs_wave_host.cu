@@ -90,11 +90,11 @@ WavePlan plan_wave(int64_t m, int64_t n, int64_t k, int kmax, int nbt, int K_req
 }
 
 // ---- launch -------------------------------------------------------------------
-template <typename T, int KMAX, int NBT, int WARPS, int INTMUL>
+template <typename T, int KMAX, int NBT, int WARPS, int OP>
 static cudaError_t launch_wave(const WaveProblem& P, const CUtensorMap& map, cudaStream_t stream,
                                int ctas_per_sm_req) {
   using SM = WaveSmem<T, KMAX, NBT>;
-  auto kfn = wave_kernel<T, KMAX, NBT, WARPS, INTMUL>;
+  auto kfn = wave_kernel<T, KMAX, NBT, WARPS, OP>;
   const int smem = WARPS * SM::kWarpBytes;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
@@ -167,16 +167,18 @@ rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const 
     P.ticket = reinterpret_cast<unsigned long long*>(base + tick_off);
     P.status = reinterpret_cast<int*>(base + tick_off + 64);
     P.total = pl.total;
-    const int tr = trace_begin(sizeof(T) == 8 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32,
+    const int tr = trace_begin(opt.reflectors ? ROT_KERNEL_REFLECT_F64
+                               : sizeof(T) == 8 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32,
                                (long long)m * (n - 1) * k, stream);
     const int prod = opt.fp64_products ? opt.fp64_products : kDefaultFp64Products;
     cudaError_t le;
     if constexpr (sizeof(T) == 8) {
-      if (prod == 2) le = launch_wave<T, KMAX, kNBT, kWarps, 2>(P, map, stream, opt.ctas_per_sm);
-      else le = launch_wave<T, KMAX, kNBT, kWarps, 1>(P, map, stream, opt.ctas_per_sm);
+      if (opt.reflectors) le = launch_wave<T, KMAX, kNBT, kWarps, kOpReflect>(P, map, stream, opt.ctas_per_sm);
+      else if (prod == 2) le = launch_wave<T, KMAX, kNBT, kWarps, kOpRotateIntmul>(P, map, stream, opt.ctas_per_sm);
+      else le = launch_wave<T, KMAX, kNBT, kWarps, kOpRotate>(P, map, stream, opt.ctas_per_sm);
     } else {
       (void)prod;
-      le = launch_wave<T, KMAX, kNBT, kWarps, 1>(P, map, stream, opt.ctas_per_sm);
+      le = launch_wave<T, KMAX, kNBT, kWarps, kOpRotate>(P, map, stream, opt.ctas_per_sm);
     }
     trace_end(tr, stream);
     if (le != cudaSuccess) { st = ROT_ECUDA; break; }
@@ -267,6 +269,62 @@ rot_status wave_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda
     count_launches(2);
   } while (0);
   cudaFreeAsync(scratch, stream);
+  return st;
+}
+
+// Fault-detection self-test: the FP64 wave kernel on a small problem whose
+// ticket counter starts past the first wave-block of every chain, so the
+// items handed out wait on counters that nothing will advance.  Their bounded
+// waits run out after wait_ms, record a timeout in the status word and the
+// kernel returns; nothing faults or traps, and the context stays usable.
+rot_status selftest_dependency_timeout(int wait_ms, cudaStream_t stream, int* device_status) {
+  const int64_t m = 64, n = 256, k = 4;
+  const WavePlan pl = plan_wave(m, n, k, 16, kNBT, 0, 0, 8, 32);
+  const int64_t W2 = 2 * (int64_t)pl.kpad;
+  const size_t a_bytes = (size_t)m * n * sizeof(double);
+  const size_t cs_bytes = (size_t)pl.cs_rows * W2 * sizeof(double);
+  const size_t cs_off = round_up(a_bytes, 256);
+  const size_t done_off = round_up(cs_off + cs_bytes, 256);
+  const size_t tick_off = round_up(done_off + (size_t)pl.nchains * pl.G * sizeof(int), 256);
+  const size_t total = tick_off + 256;
+  unsigned char* base = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&base, total, stream);
+  if (e != cudaSuccess) return cuda_failed(e, "selftest: allocation");
+  rot_status st = ROT_OK;
+  do {
+    e = cudaMemsetAsync(base, 0, total, stream);
+    if (e != cudaSuccess) { st = cuda_failed(e, "selftest: memset"); break; }
+    // Start the tickets after key 0: every chain's first item (b = 0, g = 0)
+    // is never handed out, so its dependants wait in vain.
+    const unsigned long long first = (unsigned long long)pl.nchains;
+    e = cudaMemcpyAsync(base + tick_off, &first, sizeof first, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) { st = cuda_failed(e, "selftest: ticket"); break; }
+    CUtensorMap map;
+    if (!encode_tile_map_2d(&map, base + cs_off, true, (uint64_t)W2, (uint64_t)pl.cs_rows,
+                            (uint64_t)W2 * sizeof(double), 2 * 16, kNBT)) {
+      note_error("selftest: cuTensorMapEncodeTiled failed");
+      st = ROT_ECUDA;
+      break;
+    }
+    WaveProblem P{};
+    P.A = base; P.lda = m; P.m = (int)m; P.n = (int)n; P.k = (int)k;
+    P.K = pl.K; P.NB = pl.NB; P.delta = pl.delta; P.nchains = pl.nchains; P.G = pl.G; P.B = pl.B;
+    set_full_range(P);
+    P.done = reinterpret_cast<int*>(base + done_off);
+    P.ticket = reinterpret_cast<unsigned long long*>(base + tick_off);
+    P.status = reinterpret_cast<int*>(base + tick_off + 64);
+    P.total = pl.total;
+    P.wait_ns = (unsigned long long)wait_ms * 1000000ull;
+    e = launch_wave<double, 16, kNBT, kWarps, kOpRotate>(P, map, stream, 1);
+    if (e != cudaSuccess) { st = cuda_failed(e, "selftest: launch"); break; }
+    int hs = 0;
+    e = cudaMemcpyAsync(&hs, P.status, sizeof hs, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) { st = cuda_failed(e, "selftest: status"); break; }
+    *device_status = hs;
+  } while (0);
+  cudaFreeAsync(base, stream);
+  cudaStreamSynchronize(stream);
   return st;
 }
 

@@ -179,3 +179,17 @@ def test_f64_paper_shaped_8192_sampled_rows(rs):
     n0 = torch.from_numpy(np.linalg.norm(A, axis=1)).cuda()
     n1 = torch.linalg.norm(Ad, dim=1)
     assert float(((n1 - n0).abs() / n0).max()) <= 8 * k * 2.0 ** -53 * 4
+
+
+@pytest.mark.parametrize("m,n,k", SHAPES)
+def test_reflectors_bit_exact(rs, m, n, k):
+    from paper_2412_01852_gb300 import api
+    A = wl.matrix(m, n, seed=m + n + k)
+    T, V = wl.reflectors(n, k, seed=m * 3 + k)
+    ref = oracle.refl_sequence(A, T, V)
+    Ad, _ = to_dev(A)
+    Td, _ = to_dev(T)
+    Vd, _ = to_dev(V)
+    api.rot_apply_reflectors(Ad, Td, Vd)
+    rs.rot_device_status()
+    assert np.array_equal(bits(Ad.cpu().numpy()), bits(ref))
