@@ -19,6 +19,7 @@ Functions and the passages they follow:
 * ``rot_sequence_gemm``       -- Algorithm 2 regrouped into accumulated blocks applied
                                  by FP64 matrix products (rs_gemm, Section 8).
 * ``refl_sequence``           -- 2x2 reflectors (tau, nu) in Algorithm 2's order (Section 6).
+* ``rot_sequence_left``       -- the rotations applied to rows (Algorithm 2 on A^T).
 * ``refl_sequence_reverse``   -- the same reflectors in reverse order (their inverse).
 
 Parity status: every function is pinned by ``tests/test_oracle_pins.py`` (closed
@@ -62,7 +63,8 @@ def _declare(lib):
     """Attach argument types to a loaded oracle library."""
     seq = [_i64, _i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
     for name in ("oracle_rot_sequence", "oracle_rot_sequence_wavefront",
-                 "oracle_rot_sequence_inverse", "oracle_refl_sequence", "oracle_refl_sequence_reverse"):
+                 "oracle_rot_sequence_inverse", "oracle_refl_sequence", "oracle_refl_sequence_reverse",
+                 "oracle_rot_sequence_left"):
         getattr(lib, name).argtypes = seq
         getattr(lib, name).restype = None
     lib.oracle_rot_sequence_f32.argtypes = [_i64, _i64, _i64, _fp, _i64, _fp, _i64, _fp, _i64]
@@ -147,6 +149,24 @@ def rot(x, y, c, s):
 def rot_sequence(A, C, S):
     """Algorithm 2: A * G(0,0) G(1,0) ... G(n-2,k-1), FP64."""
     return _run_seq("oracle_rot_sequence", A, C, S)
+
+
+def rot_sequence_left(A, C, S):
+    """Rotations on rows j, j+1 of A (C, S are (m-1) x k): Algorithm 2 on A^T, transposed back."""
+    lib = _load()
+    A = _fortran(A, np.float64)
+    C = _fortran(C, np.float64)
+    S = _fortran(S, np.float64)
+    m, n = A.shape
+    k = C.shape[1] if C.ndim == 2 else 0
+    if n == 0 or m < 2 or k == 0:
+        return A
+    if C.shape[0] != m - 1 or S.shape != C.shape:
+        raise ValueError("C and S must be (m-1) x k")
+    lib.oracle_rot_sequence_left(m, n, k, _ptr(A, ctypes.c_double), max(1, m),
+                                 _ptr(C, ctypes.c_double), max(1, m - 1),
+                                 _ptr(S, ctypes.c_double), max(1, m - 1))
+    return A
 
 
 def refl_sequence(A, T, V):

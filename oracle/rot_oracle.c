@@ -217,3 +217,27 @@ void oracle_refl_sequence_reverse(int64_t m, int64_t n, int64_t k,
         for (int64_t j = n - 2; j >= 0; --j)
             refl_f64(m, A + j * lda, A + (j + 1) * lda, T[j + p * ldt], V[j + p * ldv]);
 }
+
+/*
+ * Rotations applied from the left, to rows: for p = 0..k-1, j = 0..m-2,
+ * Algorithm 1 on the row vectors x = A(j,:), y = A(j+1,:) with
+ * (c, s) = (C(j,p), S(j,p)); C and S are (m-1) x k.  This is Algorithm 2 on
+ * A^T, written directly on the rows of the column-major A.
+ */
+void oracle_rot_sequence_left(int64_t m, int64_t n, int64_t k,
+                              double *A, int64_t lda,
+                              const double *C, int64_t ldc,
+                              const double *S, int64_t lds)
+{
+    for (int64_t p = 0; p < k; ++p)
+        for (int64_t j = 0; j + 1 < m; ++j) {
+            double c = C[j + p * ldc], s = S[j + p * lds];
+            for (int64_t i = 0; i < n; ++i) {
+                double xi = A[j + i * lda], yi = A[j + 1 + i * lda];
+                double sy = s * yi;
+                double sx = s * xi;
+                A[j + i * lda] = fma(c, xi, sy);
+                A[j + 1 + i * lda] = fma(c, yi, -sx);
+            }
+        }
+}

@@ -38,6 +38,8 @@ PINS = [
     pins.test_reflector_is_an_involution_and_reverse_undoes_a_sequence,
     pins.test_reflectors_orthogonal_and_norm_preserving,
     pins.test_reflector_matches_matrix_definition,
+    lambda: pins.test_left_application_is_the_transpose_of_right_application(33, 17, 12),
+    pins.test_left_application_orthogonal_and_golden,
 ]
 
 # (name, text to find, replacement, occurrence index among matches)
@@ -65,6 +67,9 @@ MUTANTS = [
     ("refl_sign", "y[i] = fma(-nu, w, yi);", "y[i] = fma(nu, w, yi);", 0),
     ("refl_dropped", "double t = fma(nu, yi, xi);", "double t = xi;", 0),
     ("refl_tau", "double w = tau * t;", "double w = nu * t;", 0),
+    ("left_rows", "double xi = A[j + i * lda], yi = A[j + 1 + i * lda];",
+     "double xi = A[j + i * lda], yi = A[j + (i + 1) % n * lda];", 0),
+    ("left_sign", "A[j + 1 + i * lda] = fma(c, yi, -sx);", "A[j + 1 + i * lda] = fma(c, yi, sx);", 0),
 ]
 
 

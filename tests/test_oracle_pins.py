@@ -332,3 +332,25 @@ def test_reflector_matches_matrix_definition():
     H = np.eye(2) - tau * np.outer([1.0, nu], [1.0, nu])
     out = oracle.refl_sequence(A, T, V)
     assert np.max(np.abs(out - A @ H)) <= 16 * U64 * np.abs(A).max()
+
+
+# ------------------------------------------------------- rotations from the left
+@pytest.mark.parametrize("m,n,k", [(2, 3, 1), (9, 5, 4), (33, 17, 12), (40, 1, 3)])
+def test_left_application_is_the_transpose_of_right_application(m, n, k):
+    """Rotating rows of A equals Algorithm 2 on A^T, bit for bit (same operations per element)."""
+    A = wl.matrix(m, n, seed=80 + m)
+    C, S = wl.rotations(m, k, seed=81 + k)
+    left = oracle.rot_sequence_left(A, C, S)
+    right = oracle.rot_sequence(np.asfortranarray(A.T), C, S).T
+    assert np.array_equal(left.view(np.uint64), np.ascontiguousarray(right).view(np.uint64))
+
+
+def test_left_application_orthogonal_and_golden():
+    # rows of the golden signed permutation example become columns of A^T
+    g = read_golden("signed_permutation_2x4.txt")
+    A = np.array(g["A"]).T            # 4 x 2: rotations now act on rows
+    out = oracle.rot_sequence_left(A, np.array(g["C"]), np.array(g["S"]))
+    assert np.array_equal(out, np.array(g["R"]).T)
+    C, S = wl.rotations(30, 9, seed=82)
+    Q = oracle.rot_sequence_left(np.eye(30), C, S)
+    assert np.linalg.norm(Q @ Q.T - np.eye(30)) <= 16 * 30 * 9 * U64
