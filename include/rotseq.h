@@ -94,6 +94,21 @@ rot_status rot_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda,
                          int64_t ldc, const float* S, int64_t lds, void* stream);
 
 /*
+ * The rotations applied from the left, to rows: for p = 0..k-1 and
+ * j = 0..m-2, rows j and j+1 of A (m x n, column-major) are replaced by
+ *     A(j,:)   <-  c*A(j,:) + s*A(j+1,:)
+ *     A(j+1,:) <- -s*A(j,:) + c*A(j+1,:)      with c = C(j,p), s = S(j,p),
+ * i.e. Algorithm 2 on A^T (A <- (A^T G(0,0) ... G(m-2,k-1))^T).  C and S are
+ * (m-1) x k with leading dimensions ldc, lds >= max(1, m-1).  Bit-identical
+ * to a plain loop over rows with the same FMA placement.  Implemented as a
+ * transpose into scratch, the column kernel and a transpose back; the scratch
+ * (m*n doubles) comes from the stream-ordered allocator.  Quick return when
+ * n == 0, m <= 1 or k == 0.
+ */
+rot_status rot_apply_left(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
+                          int64_t ldc, const double* S, int64_t lds, void* stream);
+
+/*
  * 2x2 reflectors in place of rotations (Section 6): for p = 0..k-1 and
  * j = 0..n-2 in Algorithm 2's order, columns j and j+1 of A are multiplied
  * by the reflector H = I - tau*v*v^T with v = (1, nu), tau = T(j,p),

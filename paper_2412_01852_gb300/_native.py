@@ -32,6 +32,7 @@ SIGNATURES = {
     "rot_selftest_wait_timeout": (ci, [ci, vp]),
     "rot_apply_host": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_reflectors": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "rot_apply_left": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_noalloc": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_trace_start": (ci, []),
     "rot_trace_stop": (ci, [vp, ci, ctypes.POINTER(ci)]),

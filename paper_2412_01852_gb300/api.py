@@ -353,3 +353,19 @@ def rot_apply_reflectors(A, T, V, stream=None):
     _native.check(lib.rot_apply_reflectors(*_args(A, T, V, torch.float64), _stream_handle(stream)),
                   "rot_apply_reflectors")
     return A
+
+
+def rot_apply_left(A, C, S, stream=None):
+    """Rotations on rows j, j+1 of A (column-major m x n); C, S are (m-1) x k device tensors."""
+    lib = _native.load()
+    for name, t in (("A", A), ("C", C), ("S", S)):
+        if t.dtype != torch.float64:
+            raise TypeError("%s must be float64" % name)
+    m, n = A.shape
+    mm1 = max(m - 1, 0)
+    if C.shape != S.shape or (m >= 2 and C.shape[0] != mm1):
+        raise ValueError("C and S must both be (m-1) x k")
+    k = C.shape[1]
+    _native.check(lib.rot_apply_left(m, n, k, _ptr(A), _ld(A, m), _ptr(C), _ld(C, mm1), _ptr(S), _ld(S, mm1),
+                                     _stream_handle(stream)), "rot_apply_left")
+    return A

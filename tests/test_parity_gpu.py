@@ -193,3 +193,21 @@ def test_reflectors_bit_exact(rs, m, n, k):
     api.rot_apply_reflectors(Ad, Td, Vd)
     rs.rot_device_status()
     assert np.array_equal(bits(Ad.cpu().numpy()), bits(ref))
+
+
+@pytest.mark.parametrize("m,n,k,lda", [(2, 3, 1, 2), (77, 100, 21, 77), (130, 257, 17, 131),
+                                       (300, 64, 48, 301), (17, 1, 5, 17), (64, 2000, 3, 64)])
+def test_left_application_bit_exact(rs, m, n, k, lda):
+    from paper_2412_01852_gb300 import api
+    A = wl.matrix(m, n, seed=m + n)
+    C, S = wl.rotations(m, k, seed=k + 5)
+    ref = oracle.rot_sequence_left(A, C, S)
+    Ad, Abuf = to_dev(A, lda)
+    Cd, _ = to_dev(C)
+    Sd, _ = to_dev(S)
+    before = Abuf.cpu().numpy().copy()
+    api.rot_apply_left(Ad, Cd, Sd)
+    rs.rot_device_status()
+    after = Abuf.cpu().numpy()
+    assert np.array_equal(bits(after[:m]), bits(ref))
+    assert np.array_equal(bits(after[m:]), bits(before[m:]))
