@@ -320,9 +320,14 @@ typedef struct {
  * free, puts everything admitted in that step (at most max_batch) into one
  * launch of the batched wavefront kernel, and issues it on a free stream;
  * launches on different streams overlap on the device.  A matrix is never in
- * two launches at once, so requests on one matrix apply in submission order.
- * The paper has no serving layer; every request computes Algorithm 2 on its
- * matrix exactly as rot_apply would (bit-identical results).
+ * two launches at once, so requests on one matrix apply in submission order;
+ * consecutive pending requests on one matrix (up to 64 sequences together)
+ * go out as one problem whose sequences are theirs in submission order, which
+ * is the same computation.  A launch's grid is sized to the work items it can
+ * run at once, leaving SMs to the launches beside it, and a launch with few
+ * items per key uses p-blocks of 8 or 4 sequences.  The paper has no serving
+ * layer; every request computes Algorithm 2 on its matrix exactly as
+ * rot_apply would (bit-identical results).
  */
 rot_status rot_server_create(const rot_server_config* cfg, rot_server** server);
 

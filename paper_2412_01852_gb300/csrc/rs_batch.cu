@@ -97,6 +97,7 @@ rot_status batch_layout(int count, const rot_problem* probs, const rot_tuning& t
   }
   // Segment table: keys in increasing order, instances in order within a key.
   for (int kappa = 0; kappa <= max_key && ni > 0; ++kappa) {
+    long long in_key = 0;
     for (int t = 0; t < ni; ++t) {
       int glo;
       const WavePlan& pl = L->wp[t];
@@ -104,7 +105,9 @@ rot_status batch_layout(int count, const rot_problem* probs, const rot_tuning& t
       if (pairs <= 0) continue;
       L->seg.push_back(WaveSegment{L->tickets, t, kappa});
       L->tickets += (long long)pairs * pl.nchains;
+      in_key += (long long)pairs * pl.nchains;
     }
+    L->key_items_max = std::max(L->key_items_max, in_key);
   }
   size_t off = 0;
   auto take = [&](size_t bytes, size_t align) {
@@ -170,6 +173,7 @@ rot_status batch_image(const BatchLayout& L, const rot_problem* probs, unsigned 
   B->nseg = (int)L.seg.size();
   B->total = L.tickets;
   B->rotation_rows = L.rotation_rows;
+  B->key_items_max = L.key_items_max;
   B->repack_grid_x = (int)std::min<int64_t>(ceil_div(max_count, 256), 1024);
   return ROT_OK;
 }
@@ -198,10 +202,44 @@ rot_status batch_prepare(BatchLaunch* B) {
   if (occ < 1) return cuda_failed(cudaErrorInvalidConfiguration, "batch_prepare: occupancy 0");
   const int per_sm = B->tuning.ctas_per_sm > 0 ? std::min(B->tuning.ctas_per_sm, occ) : occ;
   long long grid = (long long)nsm * per_sm;
+  // Warps beyond ~1.5 per item of the busiest key would only wait on
+  // dependencies; leave their SMs to other launches.  (0: not known, no cap.)
+  if (B->key_items_max > 0) {
+    const long long useful = (3 * B->key_items_max + 1) / 2;
+    grid = std::min<long long>(grid, (useful + kWarps - 1) / kWarps);
+  }
   grid = std::min<long long>(grid, (B->total + kWarps - 1) / kWarps);
   B->grid = (int)std::max<long long>(grid, 1);
   B->smem = smem;
   return ROT_OK;
+}
+
+rot_status batch_resident_warps(long long* warps) {
+  auto kfn = batched_fn(kDefaultFp64Products == 2);
+  const int smem = kWarps * WaveSmem<double, kKMAX, kNBT>::kWarpBytes;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_failed(e, "batch_resident_warps: cudaGetDevice");
+  e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_failed(e, "batch_resident_warps: cudaFuncSetAttribute");
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kWarps * 32, smem);
+  if (e != cudaSuccess) return cuda_failed(e, "batch_resident_warps: occupancy");
+  *warps = (long long)nsm * std::max(occ, 1) * kWarps;
+  return ROT_OK;
+}
+
+int batch_pick_K(int count, const rot_problem* probs, long long warps) {
+  for (int K : {16, 8}) {
+    long long items = 0;
+    for (int i = 0; i < count; ++i) {
+      const rot_problem& q = probs[i];
+      if (q.m <= 0 || q.n <= 1 || q.k <= 0) continue;
+      items += ceil_div(q.m, 32) * ceil_div(q.k, K);
+    }
+    if (items >= warps) return K;
+  }
+  return 4;
 }
 
 rot_status batch_launch_kernel(const BatchLaunch& B, cudaStream_t s, int trace_kind, long long work) {

@@ -22,6 +22,7 @@ struct BatchLayout {
   size_t o_inst = 0, o_tmap = 0, o_seg = 0, o_rep = 0, o_cnt = 0, o_cs = 0, total = 0;
   size_t cnt_bytes = 0;
   long long tickets = 0, rotation_rows = 0;
+  long long key_items_max = 0;        // most work items sharing one wavefront key
 };
 
 // Everything needed to enqueue one batched launch whose workspace is at `base`.
@@ -41,6 +42,7 @@ struct BatchLaunch {
   long long total = 0;
   int repack_grid_x = 1;
   long long rotation_rows = 0;
+  long long key_items_max = 0;        // bounds how many warps can have work at once (0: unknown)
   int grid = 1;
   int smem = 0;
   bool intmul = false;  // FP64 products on the integer pipe
@@ -56,7 +58,18 @@ rot_status batch_image(const BatchLayout& L, const rot_problem* probs, unsigned 
                        unsigned char* img, BatchLaunch* B);
 
 // Launch geometry on the current device (occupancy; not during stream capture).
+// The grid is the smaller of a full persistent grid and what the launch's
+// parallelism can use (about one warp per work item of its busiest key), so a
+// small launch leaves SMs free for launches running beside it.
 rot_status batch_prepare(BatchLaunch* B);
+
+// Warps of the batched kernel that fit on the current device at once.
+rot_status batch_resident_warps(long long* warps);
+
+// Sequences per p-block for a launch over these problems: the largest of
+// 16, 8, 4 whose p-blocks give at least `warps` work items per key summed over
+// the problems (smaller p-blocks mean more items that can run at once), else 4.
+int batch_pick_K(int count, const rot_problem* probs, long long warps);
 
 // Launch the persistent batched kernel and the status fold for a prepared
 // launch (the only place the batched kernel is launched).

@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 
 #include "rs_batch.h"
+#include "rs_gemm_tc.h"
 
 namespace rs {
 namespace {
@@ -680,7 +681,8 @@ rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t ld
   const size_t o_q = rs::round_up((int64_t)F.total, 1024);
   const size_t o_hi = rs::round_up((int64_t)(o_q + q_bytes), 1024);
   const size_t o_lo = rs::round_up((int64_t)(o_hi + split_bytes), 1024);
-  const size_t total = o_lo + split_bytes + 1024;
+  const size_t o_status = rs::round_up((int64_t)(o_lo + split_bytes), 256);
+  const size_t total = o_status + 256;
   void* ws = nullptr;
   if (cudaMallocAsync(&ws, total, s) != cudaSuccess) { cudaGetLastError(); return ROT_ENOMEM; }
   unsigned char* base = static_cast<unsigned char*>(ws);
@@ -699,7 +701,27 @@ rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t ld
     if (mode == ROT_GEMM_SPLIT_BF16) {
       rs::split_kernel<ROT_GEMM_SPLIT_BF16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
                                                                   const_cast<uint16_t*>(P.Qlo), qe);
-      e = rs::launch_apply<ROT_GEMM_SPLIT_BF16>(P, s);
+      if (rs::apply_tc_supported(L, Lp, nb)) {
+        // tcgen05: 128-row tiles, accumulator in tensor memory.
+        rs::TcApplyParams T{};
+        T.A = A; T.lda = lda; T.m = (int)m; T.n = (int)n; T.L = L; T.Lp = Lp; T.nb = nb;
+        T.nblk = (int)nblk;
+        T.c0 = P.c0;
+        T.Qhi = P.Qhi;
+        T.Qlo = P.Qlo;
+        uint32_t cols = 32;
+        while (cols < (uint32_t)Lp) cols <<= 1;
+        T.tmem_cols = cols;
+        T.status = reinterpret_cast<int*>(base + o_status);
+        e = cudaMemsetAsync(T.status, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = rs::launch_apply_tc(T, s);
+        if (e == cudaSuccess) {
+          rs::record_status_async(T.status, s);
+          rs::count_launches(1);
+        }
+      } else {
+        e = rs::launch_apply<ROT_GEMM_SPLIT_BF16>(P, s);
+      }
     } else if (mode == ROT_GEMM_SPLIT_F16) {
       rs::split_kernel<ROT_GEMM_SPLIT_F16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
                                                                  const_cast<uint16_t*>(P.Qlo), qe);

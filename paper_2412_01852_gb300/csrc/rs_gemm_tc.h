@@ -1,0 +1,30 @@
+// rs_gemm_tc.h -- the tcgen05 (TMEM-accumulator) block apply of the
+// accumulated-block variant, split BF16 (rs_gemm_tc.cu).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rs {
+
+struct TcApplyParams {
+  double* A;
+  int64_t lda;
+  int m, n;
+  int L;                  // nb + kb: window width
+  int Lp;                 // L rounded up to a multiple of 32 (Q's padded size)
+  int nb;                 // columns a window advances within a p-block
+  int nblk;
+  const int* c0;          // first window column of each block, in apply order
+  const uint16_t* Qhi;    // nblk x Lp x Lp BF16, column n holds k contiguous
+  const uint16_t* Qlo;
+  uint32_t tmem_cols;     // power of two >= Lp (the accumulator's columns)
+  int* status;            // first device error (timeouts), 0 if none
+};
+
+// Whether the tensor-core apply supports this block shape.
+bool apply_tc_supported(int L, int Lp, int nb);
+size_t apply_tc_smem_bytes(int Lp);
+cudaError_t launch_apply_tc(const TcApplyParams& P, cudaStream_t s);
+
+}  // namespace rs

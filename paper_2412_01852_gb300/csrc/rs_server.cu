@@ -134,6 +134,7 @@ struct Server {
   std::unordered_map<uint64_t, std::shared_ptr<Request>> live;  // submitted, not yet waited on
   std::vector<Launch*> finished;      // completed launches, released by the scheduler
   uint64_t next_ticket = 1;
+  long long warps = 1;                // resident warps of the batched kernel on this device
   int inflight = 0;                   // requests admitted and not completed
   bool stop = false;
   std::thread thread;
@@ -181,24 +182,42 @@ void reap_locked(Server* S) {
   S->finished.clear();
 }
 
-// Device bytes a launch over these requests needs (layout + compact C/S).
-bool size_launch(Server* S, const std::vector<std::shared_ptr<Request>>& rs_, BatchLayout* L,
-                 std::vector<rot_problem>* probs, size_t* cs_region, size_t* total) {
+// Requests on one matrix that go out together as one problem.  Their
+// sequences are concatenated in submission order: Algorithm 2 applies every
+// rotation of sequence p before any of sequence p+1, so applying request r1
+// and then r2 is the same computation, in the same order for every element,
+// as one request holding r1's sequences followed by r2's.
+struct Group {
+  int handle = -1;
+  int64_t k = 0;
+  std::vector<std::shared_ptr<Request>> reqs;
+};
+
+// Largest number of sequences fused into one problem.
+constexpr int64_t kFuseMaxK = 64;
+
+// Device bytes a launch over these groups needs (layout + compact C/S).
+bool size_launch(Server* S, const std::vector<Group>& gs, BatchLayout* L, std::vector<rot_problem>* probs,
+                 size_t* cs_region, size_t* total) {
   probs->clear();
   size_t cs = 0;
-  for (auto& r : rs_) {
-    const Matrix& M = S->mats[r->handle];
+  for (const Group& g : gs) {
+    const Matrix& M = S->mats[g.handle];
     rot_problem q{};
-    q.m = M.m; q.n = M.n; q.k = r->k; q.A = M.A; q.lda = M.lda;
+    q.m = M.m; q.n = M.n; q.k = g.k; q.A = M.A; q.lda = M.lda;
     q.C = reinterpret_cast<const double*>(0x100);  // placeholders until the arena offset is known
     q.S = reinterpret_cast<const double*>(0x100);
     q.ldc = std::max<int64_t>(1, M.n - 1);
     q.lds = q.ldc;
     probs->push_back(q);
-    cs += align256(r->cs.size() * sizeof(double));
+    cs += align256(2 * (size_t)(M.n - 1) * (size_t)g.k * sizeof(double));
   }
+  // A launch with few work items per key uses short p-blocks, so that even a
+  // lone large request keeps the whole GPU busy (its latency is the tail).
+  rot_tuning tu{};
+  tu.K = batch_pick_K((int)probs->size(), probs->data(), S->warps);
   *L = BatchLayout{};
-  if (batch_layout((int)probs->size(), probs->data(), rot_tuning{0, 0, 0}, L) != ROT_OK) return false;
+  if (batch_layout((int)probs->size(), probs->data(), tu, L) != ROT_OK) return false;
   *cs_region = align256(L->total);
   *total = *cs_region + cs;
   return true;
@@ -210,69 +229,91 @@ void scheduler(Server* S) {
   while (true) {
     reap_locked(S);
     if (S->stop && S->pending.empty() && S->inflight == 0) break;
-    // ---- form one batch from the pending queue, in submission order --------
+    // ---- form one launch from the pending queue, in submission order -------
+    // Every matrix that is not busy contributes the longest run of its
+    // pending requests that fits (slots, batch size, fused length); a matrix
+    // is never in two launches at once, so its requests keep their order.
     int free_slot = -1;
     for (size_t i = 0; i < S->slots.size(); ++i)
       if (!S->slots[i].busy) { free_slot = (int)i; break; }
-    std::vector<std::shared_ptr<Request>> batch;
+    std::vector<Group> groups;
+    int nreq = 0;
     if (free_slot >= 0 && !S->pending.empty()) {
+      std::vector<int> gidx(S->mats.size(), -1);
       std::vector<char> blocked(S->mats.size(), 0);
       for (auto it = S->pending.begin(); it != S->pending.end();) {
         auto& r = *it;
-        const bool can = !blocked[r->handle] && !S->mats[r->handle].busy &&
-                         S->inflight + (int)batch.size() < S->cfg.max_inflight &&
-                         (int)batch.size() < S->cfg.max_batch;
+        const int h = r->handle;
+        bool can = !blocked[h] && !S->mats[h].busy && S->inflight + nreq < S->cfg.max_inflight &&
+                   nreq < S->cfg.max_batch;
+        if (can && gidx[h] >= 0 && groups[gidx[h]].k + r->k > kFuseMaxK) can = false;
         if (!can) {
-          blocked[r->handle] = 1;   // later requests on this matrix keep their order
+          blocked[h] = 1;   // later requests on this matrix keep their order
           ++it;
           continue;
         }
-        batch.push_back(r);
-        blocked[r->handle] = 1;     // one request per matrix per launch
+        if (gidx[h] < 0) {
+          gidx[h] = (int)groups.size();
+          groups.push_back(Group{});
+          groups.back().handle = h;
+        }
+        groups[gidx[h]].k += r->k;
+        groups[gidx[h]].reqs.push_back(r);
+        ++nreq;
         it = S->pending.erase(it);
       }
     }
-    if (batch.empty()) {
+    if (groups.empty()) {
       if (S->stop && S->pending.empty() && S->inflight == 0) break;
       S->cv_sched.wait_for(lk, std::chrono::milliseconds(2));
       continue;
     }
-    // ---- fit the batch in the arena, shrinking it if memory is short --------
+    // ---- fit the launch in the arena, returning requests if memory is short -
+    // The last request of the last group goes back first, so a group shrinks
+    // to the run of its matrix's requests that fits.
     BatchLayout L;
     std::vector<rot_problem> probs;
     size_t cs_region = 0, total = 0, off = 0;
-    while (!batch.empty()) {
-      if (size_launch(S, batch, &L, &probs, &cs_region, &total) && S->arena->alloc(total, &off)) break;
-      S->pending.push_front(batch.back());  // back to the head of the queue
-      batch.pop_back();
+    while (!groups.empty()) {
+      if (size_launch(S, groups, &L, &probs, &cs_region, &total) && S->arena->alloc(total, &off)) break;
+      Group& g = groups.back();
+      S->pending.push_front(g.reqs.back());  // back to the queue
+      g.k -= g.reqs.back()->k;
+      g.reqs.pop_back();
+      --nreq;
+      if (g.reqs.empty()) groups.pop_back();
     }
-    if (batch.empty()) {                    // nothing fits now: wait for memory
-      S->cv_sched.wait_for(lk, std::chrono::milliseconds(2));
-      continue;
-    }
-    // Re-sort the requests returned to the queue by ticket (submission order).
+    // Restore submission order in the queue (ticket order).
     std::sort(S->pending.begin(), S->pending.end(),
               [](const std::shared_ptr<Request>& a, const std::shared_ptr<Request>& b) {
                 return a->ticket < b->ticket;
               });
-    for (auto& r : batch) S->mats[r->handle].busy = true;
-    S->inflight += (int)batch.size();
+    if (groups.empty()) {                   // nothing fits now: wait for memory
+      S->cv_sched.wait_for(lk, std::chrono::milliseconds(2));
+      continue;
+    }
+    std::vector<std::shared_ptr<Request>> all;
+    for (auto& g : groups) {
+      S->mats[g.handle].busy = true;
+      all.insert(all.end(), g.reqs.begin(), g.reqs.end());
+    }
+    S->inflight += nreq;
     Slot& slot = S->slots[free_slot];
     slot.busy = true;
     S->launches += 1;
-    S->batched_requests += (int64_t)batch.size();
+    S->batched_requests += nreq;
     lk.unlock();
 
     // ---- build and enqueue the launch (no lock held) ------------------------
     unsigned char* base = S->arena_base + off;
     size_t coff = cs_region;
     std::vector<size_t> cs_at;
-    for (size_t i = 0; i < batch.size(); ++i) {
+    for (size_t i = 0; i < groups.size(); ++i) {
       const size_t nm1k = (size_t)(probs[i].n - 1) * probs[i].k;
       probs[i].C = reinterpret_cast<const double*>(base + coff);
       probs[i].S = reinterpret_cast<const double*>(base + coff) + nm1k;
       cs_at.push_back(coff);
-      coff += align256(batch[i]->cs.size() * sizeof(double));
+      coff += align256(2 * nm1k * sizeof(double));
     }
     const size_t stage_need = total + 256;
     rot_status st = ROT_OK;
@@ -288,7 +329,7 @@ void scheduler(Server* S) {
     launch->slot = free_slot;
     launch->arena_off = off;
     launch->arena_bytes = total;
-    launch->reqs = batch;
+    launch->reqs = all;
     BatchLaunch B;
     if (st == ROT_OK) {
       launch->status_host = reinterpret_cast<volatile int*>(slot.staging + total);
@@ -296,9 +337,19 @@ void scheduler(Server* S) {
       st = batch_image(L, probs.data(), base, slot.staging, &B);
     }
     if (st == ROT_OK) {
-      for (size_t i = 0; i < batch.size(); ++i) {
-        std::memcpy(slot.staging + cs_at[i], batch[i]->cs.data(), batch[i]->cs.size() * sizeof(double));
-        std::vector<double>().swap(batch[i]->cs);  // staged: the host copy is no longer needed
+      // Stage each group's C (then S) as the concatenation of its requests'.
+      for (size_t i = 0; i < groups.size(); ++i) {
+        const size_t nm1 = (size_t)(probs[i].n - 1);
+        double* c_dst = reinterpret_cast<double*>(slot.staging + cs_at[i]);
+        double* s_dst = c_dst + nm1 * (size_t)probs[i].k;
+        for (auto& r : groups[i].reqs) {
+          const size_t part = nm1 * (size_t)r->k;
+          std::memcpy(c_dst, r->cs.data(), part * sizeof(double));
+          std::memcpy(s_dst, r->cs.data() + part, part * sizeof(double));
+          c_dst += part;
+          s_dst += part;
+          std::vector<double>().swap(r->cs);  // staged: the host copy is no longer needed
+        }
       }
       B.device = S->device;
       st = batch_prepare(&B);
@@ -320,7 +371,7 @@ void scheduler(Server* S) {
     if (st != ROT_OK) {
       // The launch could not be issued: finish its requests with the error.
       const double t = now_s();
-      for (auto& r : batch) {
+      for (auto& r : all) {
         r->status = st;
         r->done = true;
         r->t_done = t;
@@ -359,6 +410,11 @@ rot_status rot_server_create(const rot_server_config* cfg, rot_server** out) {
   if (cudaMalloc(&a, cfg->hbm_budget_bytes) != cudaSuccess) { cudaGetLastError(); delete h; return ROT_ENOMEM; }
   S.arena_base = static_cast<unsigned char*>(a);
   S.arena.reset(new rs::Arena(cfg->hbm_budget_bytes));
+  if (rs::batch_resident_warps(&S.warps) != ROT_OK) {
+    cudaFree(a);
+    delete h;
+    return ROT_ECUDA;
+  }
   S.slots.resize(cfg->streams);
   for (auto& sl : S.slots) {
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -411,7 +467,10 @@ rot_status rot_server_submit(rot_server* srv, int handle, int64_t k, const doubl
     rs::BatchLayout L;
     std::vector<rot_problem> probs;
     size_t csr = 0, total = 0;
-    std::vector<std::shared_ptr<rs::Request>> one{r};
+    std::vector<rs::Group> one(1);
+    one[0].handle = handle;
+    one[0].k = k;
+    one[0].reqs.push_back(r);
     std::lock_guard<std::mutex> lk(S.mu);
     if (!rs::size_launch(&S, one, &L, &probs, &csr, &total) || total > S.arena->capacity()) {
       S.rejected += 1;

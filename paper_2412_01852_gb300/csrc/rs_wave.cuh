@@ -238,8 +238,12 @@ __global__ void repack_cs_kernel(const T* __restrict__ C, int64_t ldc, const T* 
 template <typename T, int KMAX, int NBT>
 struct WaveSmem {
   static constexpr int kTileElems = NBT * 2 * KMAX;              // one buffer
-  static constexpr int kTileBytes = kTileElems * (int)sizeof(T);
+  static constexpr int kBoxBytes = kTileElems * (int)sizeof(T);   // bytes one TMA copy delivers
+  // A TMA destination in shared memory must be 128-byte aligned, so each
+  // buffer occupies a whole number of 128-byte lines.
+  static constexpr int kTileBytes = (kBoxBytes + 127) / 128 * 128;
   static constexpr int kWarpBytes = 2 * kTileBytes + 128;         // 2 buffers + barriers
+  static_assert(kWarpBytes % 128 == 0, "per-warp tile buffers must stay 128-byte aligned");
 };
 
 // Per-warp shared-memory resources: two (c,s) tile buffers and their mbarriers.
@@ -339,14 +343,14 @@ __device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap
   const int ty0 = I.cs_row0 + w0 + p0;
   if (lane == 0) {
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&wt.bar[0], SM::kTileBytes);
+    mbar_arrive_expect_tx(&wt.bar[0], SM::kBoxBytes);
     tma_load_2d(wt.tile(0), tmap, &wt.bar[0], tx, ty0);
   }
   for (int st = 0; st < ntiles; ++st) {
     const int cur = st & 1;
     if (st + 1 < ntiles && lane == 0) {
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&wt.bar[cur ^ 1], SM::kTileBytes);
+      mbar_arrive_expect_tx(&wt.bar[cur ^ 1], SM::kBoxBytes);
       tma_load_2d(wt.tile(cur ^ 1), tmap, &wt.bar[cur ^ 1], tx, ty0 + (st + 1) * NBT);
     }
     const uint32_t ph = cur ? wt.phase1 : wt.phase0;

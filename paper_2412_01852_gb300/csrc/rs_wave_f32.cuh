@@ -3,13 +3,15 @@
 // Same work decomposition, ticket order, dependency counters and TMA-staged
 // (c,s) tiles as the FP64 kernel (rs_wave.cuh), shaped for FP32 speed, where
 // the rotation's 4 FP32 instructions are cheap and bookkeeping is not:
-//   * R = 2 rows per lane (a chain is 64 rows), so each (c,s) pair loaded from
-//     shared memory serves two rotations;
-//   * tiles of KMAX+1 = 17 waves.  A tile whose waves are all interior (every
+//   * R rows per lane (a chain is 32R rows), so each (c,s) pair loaded from
+//     shared memory serves R rotations;
+//   * tiles of KMAX+1 waves.  A tile whose waves are all interior (every
 //     rotation of the wave exists, every column load and store is in range)
 //     runs fully unrolled with the register window rotated by static indices:
-//     after the 17 waves the window is back in its canonical order, so no
-//     register moves, no per-rotation branches;
+//     after KMAX+1 waves the window is back in its canonical order, so no
+//     register moves, no per-rotation branches.  The unrolled tile has to fit
+//     the instruction cache, which bounds KMAX;
+//   * the columns of the next tile are loaded one tile ahead;
 //   * edge tiles (startup and shutdown triangles, short p-blocks, the ragged
 //     last item) use the generic per-wave code with a shifted window.
 // Both paths keep the window canonical at tile boundaries:
@@ -61,8 +63,14 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
     arow[r] = reinterpret_cast<T*>(I.A) + row;
   }
   const int own_lo = w0 - kr + 1;
+  // Columns enter the window one per wave (column w+1 at wave w).  At FP32
+  // speed a wave is ~100 issue cycles, shorter than an L2 round trip, so the
+  // U columns of the next tile are loaded one tile ahead into `pre`:
+  // pre[r][u] holds column ws+u+1 when tile ws starts.  Only columns <= w1 are
+  // loaded: the dependency wait above made exactly those final.
+  const int col_hi = min(w1, n - 1);
   T win[R][KMAX + 1];
-  T nextcol[R];
+  T pre[R][U];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
 #pragma unroll
@@ -71,7 +79,11 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
       win[r][s] = (rowok[r] && q >= own_lo && q >= 0 && q <= n - 1) ? ld_cg(arow[r] + (int64_t)q * lda) : T(0);
     }
     win[r][KMAX] = T(0);
-    nextcol[r] = (rowok[r] && w0 + 1 <= n - 1) ? ld_cg(arow[r] + (int64_t)(w0 + 1) * lda) : T(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = w0 + 1 + u;
+      pre[r][u] = (rowok[r] && q <= col_hi) ? ld_cg(arow[r] + (int64_t)q * lda) : T(0);
+    }
   }
 
   const int ntiles = (w1 - w0 + NBT - 1) / NBT;
@@ -79,14 +91,14 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
   const int ty0 = I.cs_row0 + w0 + p0;
   if (lane == 0) {
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&wt.bar[0], SM::kTileBytes);
+    mbar_arrive_expect_tx(&wt.bar[0], SM::kBoxBytes);
     tma_load_2d(wt.tile(0), tmap, &wt.bar[0], tx, ty0);
   }
   for (int st = 0; st < ntiles; ++st) {
     const int cur = st & 1;
     if (st + 1 < ntiles && lane == 0) {
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&wt.bar[cur ^ 1], SM::kTileBytes);
+      mbar_arrive_expect_tx(&wt.bar[cur ^ 1], SM::kBoxBytes);
       tma_load_2d(wt.tile(cur ^ 1), tmap, &wt.bar[cur ^ 1], tx, ty0 + (st + 1) * NBT);
     }
     const uint32_t ph = cur ? wt.phase1 : wt.phase0;
@@ -111,10 +123,11 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int w = ws + u;
+        const int qn = w + U + 1;            // this slot's column in the next tile
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          win[r][(KMAX + u) % U] = nextcol[r];
-          nextcol[r] = rowok[r] ? ld_cg(arow[r] + (int64_t)(w + 2) * lda) : T(0);
+          win[r][(KMAX + u) % U] = pre[r][u];
+          pre[r][u] = (rowok[r] && qn <= col_hi) ? ld_cg(arow[r] + (int64_t)qn * lda) : T(0);
         }
         const V2* trow = tl + u * KMAX;
 #pragma unroll
@@ -130,11 +143,14 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
           if (rowok[r]) st_cg(arow[r] + (int64_t)q * lda, win[r][u % U]);
       }
     } else {
+      T nextcol[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) nextcol[r] = pre[r][0];
       for (int w = ws; w < wend; ++w) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           win[r][KMAX] = nextcol[r];
-          nextcol[r] = (rowok[r] && w + 2 <= n - 1) ? ld_cg(arow[r] + (int64_t)(w + 2) * lda) : T(0);
+          nextcol[r] = (rowok[r] && w + 2 <= col_hi) ? ld_cg(arow[r] + (int64_t)(w + 2) * lda) : T(0);
         }
         const int l_lo = max(0, w - (n - 2));
         const int l_hi = min(kr - 1, w);
@@ -154,6 +170,14 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
           if (rowok[r] && q >= own_lo && q >= 0) st_cg(arow[r] + (int64_t)q * lda, win[r][0]);
 #pragma unroll
           for (int s = 0; s < KMAX; ++s) win[r][s] = win[r][s + 1];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int q = wend + 1 + u;
+          pre[r][u] = (rowok[r] && q <= col_hi) ? ld_cg(arow[r] + (int64_t)q * lda) : T(0);
         }
       }
     }
@@ -177,8 +201,8 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
 }
 
 // Single FP32 instance; same ticket decode as wave_kernel.
-template <int KMAX, int R, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1)
+template <int KMAX, int R, int WARPS, int MINB = 1>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
 wave_f32_kernel(const __grid_constant__ CUtensorMap tmap, const WaveProblem P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;

@@ -190,15 +190,20 @@ rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const 
   return st;
 }
 
-// FP32: 64-row chains (2 rows per lane), 17-wave tiles, 4 tiles per item.
-static constexpr int kF32Kmax = 16;
+// FP32: 64-row chains (2 rows per lane), p-blocks of 8 sequences, 9-wave
+// tiles, 4 tiles per item, 2 CTAs of 8 warps per SM.  Measured on GB300
+// (A 8192x8192, k = 192): this shape 3.72 ms; 16-sequence p-blocks with
+// 17-wave tiles 4.88 ms (their unrolled tile no longer fits the instruction
+// cache); 12-sequence 3.91 ms; 4 rows per lane 4.04 ms.
+static constexpr int kF32Kmax = 8;
 static constexpr int kF32R = 2;
 static constexpr int kF32NBT = kF32Kmax + 1;
+static constexpr int kF32MinBlocks = 2;
 
 static cudaError_t launch_wave_f32(const WaveProblem& P, const CUtensorMap& map, cudaStream_t stream,
                                    int ctas_per_sm_req) {
   using SM = WaveSmem<float, kF32Kmax, kF32NBT>;
-  auto kfn = wave_f32_kernel<kF32Kmax, kF32R, kWarps>;
+  auto kfn = wave_f32_kernel<kF32Kmax, kF32R, kWarps, kF32MinBlocks>;
   const int smem = kWarps * SM::kWarpBytes;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;

@@ -139,6 +139,21 @@ def test_f32_bit_exact_and_error_bound(rs, m, n, k):
     assert rel.max() <= 8 * k * U32
 
 
+@pytest.mark.parametrize("m,n,k", [(1000, 2000, 40), (4100, 700, 37), (129, 1500, 16)])
+def test_f32_many_items_bit_exact(rs, m, n, k):
+    """FP32 over many work items per chain: columns handed between items and
+    tiles, several p-blocks in flight, a ragged last chain and wave-block."""
+    A, C, S = wl.problem(m, n, k, seed=m + n + 11 * k)
+    A32, C32, S32 = A.astype(np.float32), C.astype(np.float32), S.astype(np.float32)
+    ref32 = oracle.rot_sequence_f32(A32, C32, S32)
+    Ad, _ = to_dev(A32)
+    Cd, _ = to_dev(C32)
+    Sd, _ = to_dev(S32)
+    rs.rot_apply_f32(Ad, Cd, Sd)
+    rs.rot_device_status()
+    assert np.array_equal(bits(Ad.cpu().numpy()), bits(ref32))
+
+
 @pytest.mark.parametrize("products", [1, 2])
 @pytest.mark.parametrize("m,n,k", [(100, 77, 21), (257, 130, 17), (64, 300, 48), (33, 17, 5)])
 def test_f64_products_on_either_pipe_bit_exact(rs, m, n, k, products):

@@ -85,6 +85,26 @@ def test_budget_refusal_and_serialisation(api):
     assert np.array_equal(bits(Ad.cpu().numpy()), bits(exp))
 
 
+def test_fused_requests_on_one_matrix(api):
+    """Requests queued on one matrix go out fused (their sequences concatenated);
+    the result is the same bits as applying them one after another."""
+    A = wl.matrix(300, 260, seed=9)
+    Ad = dev(A)
+    exp = A
+    with api.Server(hbm_budget_bytes=256 << 20, max_inflight=64, streams=4, max_batch=64) as srv:
+        h = srv.register(Ad)
+        reqs = [wl.rotations(260, 3 + (q * 7) % 29, seed=90 + q) for q in range(24)]
+        ts = [srv.submit(h, C, S) for (C, S) in reqs]     # a burst: later ones queue
+        for t in ts:
+            srv.wait(t, 60000)
+        st = srv.stats()
+        for (C, S) in reqs:
+            exp = oracle.rot_sequence(exp, C, S)
+        assert st["completed"] == 24
+        assert st["launches"] < 24           # queued requests were fused
+    assert np.array_equal(bits(Ad.cpu().numpy()), bits(exp))
+
+
 def test_host_wait_runs_out_then_completes(api):
     with api.Server(hbm_budget_bytes=512 << 20, max_inflight=4, streams=2, max_batch=4) as srv:
         A = dev(wl.matrix(2048, 2048, seed=4))
