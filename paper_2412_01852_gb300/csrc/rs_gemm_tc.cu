@@ -7,35 +7,41 @@
 //     A_hi*Q_hi + A_hi*Q_lo + A_lo*Q_hi
 // in one FP32 accumulator (the lo*lo term, ~2^-16 relative, is dropped).
 //
-// One CTA owns a tile of 128 rows of A and walks the blocks in their order.
-// Per block:
-//   * the window (128 rows x Lp columns) sits in shared memory as hi and lo
-//     BF16 operands in the K-major no-swizzle layout of 8x16-byte core
-//     matrices;
-//   * Q_b hi/lo (prepared in global memory, column n holding k contiguous) is
-//     streamed in chunks of 16 k-rows through two buffers (cp.async);
-//   * one thread issues, per chunk, the three products for the two halves of
-//     N (N = Lp/2 each, at most 256) and commits them to the chunk buffer's
-//     mbarrier, which releases the buffer;
-//   * the epilogue reads the accumulator (tcgen05.ld, each warp its 32-lane
-//     sub-partition), stores the block's finished columns to A in FP64 and,
-//     when the next block continues the same p-block, keeps the kb columns
-//     the two windows share in shared memory as the next window's first
-//     columns (split again from FP32), so only nb new columns are read.
-// Every wait is bounded; on a timeout the CTA records an error, stops, waits
-// for its own copies and frees its tensor memory.
+// One CTA owns a tile of 64 rows of A (M = 64) and walks the blocks in their
+// order with three roles:
+//   * a TMA producer thread streams Q_b hi/lo (prepared in global memory,
+//     column n holding k contiguous) in chunks of 16 k-rows through three
+//     stages (full/empty mbarriers);
+//   * an MMA thread issues, per chunk, the three products for the two halves
+//     of N (N = Lp/2 each, at most 256) into the TMEM accumulator and commits
+//     each chunk to its stage's empty barrier;
+//   * 16 worker warps keep two window buffers: while block b's products run
+//     they read the nb new columns of block b+1 from A (FP64), split them and
+//     write them into the other buffer; when the accumulator is complete they
+//     read it (tcgen05.ld, each warp its TMEM sub-partition), store block b's
+//     finished columns to A in FP64 and write the kb columns that blocks b
+//     and b+1 share, split again from FP32, as the next window's first
+//     columns.  The first window of a p-block is read whole, after the
+//     previous block's columns are stored.
+// The window operands sit in shared memory in the K-major no-swizzle layout
+// of 8-row x 16-byte core matrices.  Every wait is bounded; on a timeout the
+// CTA records an error, every role stops, the producer waits for its copies
+// and the tensor memory is freed.
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
 #include "rs_device.cuh"
 #include "rs_gemm_tc.h"
+#include "rs_internal.h"
 
 namespace rs {
 namespace {
 
-constexpr int kRows = 128;          // rows of A per CTA (the MMA's M)
-constexpr int kThreads = 512;
+constexpr int kRows = 64;           // rows of A per CTA (the MMA's M)
+constexpr int kWorkers = 16;        // warps that load windows and run the epilogue
+constexpr int kThreads = (2 + kWorkers) * 32;   // + the TMA producer and MMA issuer warps
+constexpr int kStages = 3;          // Q chunks in flight
 constexpr int kKChunk = 16;         // k per MMA instruction (BF16)
 constexpr uint32_t kCoreBytes = 128;  // one core matrix: 8 rows x 16 bytes
 
@@ -102,12 +108,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -125,6 +125,43 @@ __device__ __forceinline__ void split_f32(float x, uint16_t& h, uint16_t& l) {
   h = __bfloat16_as_ushort(hb);
   l = __bfloat16_as_ushort(lb);
 }
+// FP64 <-> FP32 by integer bit operations.  GB300's FP64 pipe (2 lanes per
+// clock per SM) would otherwise be this kernel's bottleneck: a conversion
+// instruction there costs as much as a DFMA.
+// FP64 -> FP32 rounding toward zero (relative error below 2^-23, far below the
+// split's 2^-17); magnitudes outside FP32's normal range go to 0 or Inf.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t sign = hi & 0x80000000u;
+  const uint32_t ed = (hi >> 20) & 0x7ffu;
+  const int e = (int)ed - 1023 + 127;
+  const uint32_t mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  uint32_t f;
+  if (ed == 0x7ffu) f = sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u);   // Inf, NaN
+  else if (e <= 0) f = sign;
+  else if (e >= 255) f = sign | 0x7f800000u;
+  else f = sign | ((uint32_t)e << 23) | mant;
+  return __uint_as_float(f);
+}
+// FP32 -> FP64, exact for zeros, normal numbers, Inf and NaN (FP32 subnormals
+// become signed zero).
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t m = u & 0x7fffffu;
+  uint32_t hi, lo = m << 29;
+  if (e == 0) { hi = sign; lo = 0; }
+  else if (e == 255) hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
+  else hi = sign | ((e + (1023u - 127u)) << 20) | (m >> 3);
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+// The window's split: x -> FP32 (by bits), then hi/lo in FP32.
+__device__ __forceinline__ void split_window(double x, uint16_t& h, uint16_t& l) {
+  split_f32(f64_to_f32_rz(x), h, l);
+}
+
 __device__ __forceinline__ uint4 pack8(const uint16_t (&e)[8]) {
   uint4 u;
   u.x = (uint32_t)e[0] | ((uint32_t)e[1] << 16);
@@ -134,60 +171,81 @@ __device__ __forceinline__ uint4 pack8(const uint16_t (&e)[8]) {
   return u;
 }
 
+// Shared-memory plan (byte offsets from the dynamic base, Lp = padded width):
+//   W[2]      two window buffers, each hi then lo, each 64 rows x Lp BF16:
+//             element (m, k) at (k/8)*1024 + m*16 + (k%8)*2
+//   Q[3]      three chunk stages, each hi then lo, each two k-groups of
+//             Lp rows x 16 bytes: element (n, k) at (k/8)*16*Lp + n*16 + (k%8)*2
+//   barriers  q_full[3], q_empty[3], w_ready[2], w_free[2], d_full, d_empty, stored
 struct Smem {
-  // byte offsets from the dynamic shared-memory base
-  uint32_t w_hi, w_lo, q, bar, slot, flag, total;
-  uint32_t q_part;   // bytes of one staged operand (hi or lo) of one buffer: Lp x 16 k
+  uint32_t w, w_buf, w_part, q, q_stage, q_part, bar, slot, flag, total;
 };
-
 __host__ __device__ inline Smem smem_plan(int Lp) {
   Smem s{};
-  const uint32_t w = (uint32_t)kRows * Lp * 2;     // one BF16 operand of the window
-  s.w_hi = 0;
-  s.w_lo = w;
-  s.q = 2 * w;
+  s.w_part = (uint32_t)kRows * Lp * 2;
+  s.w_buf = 2 * s.w_part;
+  s.w = 0;
   s.q_part = (uint32_t)Lp * kKChunk * 2;
-  s.bar = s.q + 4 * s.q_part;                       // 2 buffers x (hi, lo)
-  s.slot = s.bar + 2 * 8;
+  s.q_stage = 2 * s.q_part;
+  s.q = 2 * s.w_buf;
+  s.bar = s.q + kStages * s.q_stage;
+  s.slot = s.bar + 16 * 8;
   s.flag = s.slot + 4;
-  s.total = s.flag + 4 + 16;
+  s.total = s.flag + 4 + 8;
   return s;
 }
 
-// Write 8 consecutive window columns [k8*8, k8*8+8) of `row` (already split).
-__device__ __forceinline__ void put_window8(unsigned char* smem, const Smem& L, int row, int k8, const uint4& hi,
-                                            const uint4& lo) {
-  const uint32_t off = (uint32_t)k8 * (kRows * 16) + (uint32_t)row * 16;
-  *reinterpret_cast<uint4*>(smem + L.w_hi + off) = hi;
-  *reinterpret_cast<uint4*>(smem + L.w_lo + off) = lo;
+enum Bar { kQFull = 0, kQEmpty = 3, kWReady = 6, kWFree = 8, kDFull = 10, kDEmpty = 11, kStored = 12 };
+
+// A wait that gives up after the limit or once another role has given up.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  if (*abort_flag) return false;
+  if (mbar_wait_bounded(bar, parity)) return true;
+  set_error(status, kDevTimeoutTma);
+  *abort_flag = 1;
+  return false;
 }
 
-// Load window columns [g_lo*8, g_hi*8) of the block starting at global column
-// c0 from A (FP64), split, into the window operands.  Columns outside [0, n)
-// and rows outside [0, m) are zero; so are columns at or past L.
-__device__ void load_window(unsigned char* smem, const Smem& L, const TcApplyParams& P, int r0, int c0, int g_lo,
-                            int g_hi) {
-  const int tid = threadIdx.x;
-  const int row = tid % kRows;
+// Window columns [g_lo*8, g_hi*8) of the block whose window starts at global
+// column c0: FP64 from A, split, into buffer `wbuf`.  Columns outside [0, n),
+// at or past L, and rows outside [0, m) are zero.  `wt` is the worker thread.
+__device__ void load_window(unsigned char* smem, const Smem& S, const TcApplyParams& P, int wbuf, int wt, int r0,
+                            int c0, int g_lo, int g_hi) {
+  const int row = wt % kRows;
   const int grow = r0 + row;
   const bool rok = grow < P.m;
   const double* arow = P.A + grow;
-  for (int g = g_lo + tid / kRows; g < g_hi; g += kThreads / kRows) {
-    double v[8];
+  unsigned char* hi = smem + S.w + (uint32_t)wbuf * S.w_buf;
+  unsigned char* lo = hi + S.w_part;
+  constexpr int kStep = kWorkers * 32 / kRows;   // 8-column groups handled per pass
+  for (int g0 = g_lo + wt / kRows; g0 < g_hi; g0 += 2 * kStep) {
+    double v[2][8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int col = g * 8 + u;
-      const int gc = c0 + col;
-      v[u] = (rok && col < P.L && gc >= 0 && gc < P.n) ? __ldcg(arow + (int64_t)gc * P.lda) : 0.0;
+    for (int t = 0; t < 2; ++t) {
+      const int g = g0 + t * kStep;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int col = g * 8 + u;
+        const int gc = c0 + col;
+        v[t][u] = (g < g_hi && rok && col < P.L && gc >= 0 && gc < P.n) ? __ldcg(arow + (int64_t)gc * P.lda) : 0.0;
+      }
     }
-    uint16_t h[8], l[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) split_f64(v[u], h[u], l[u]);
-    put_window8(smem, L, row, g, pack8(h), pack8(l));
+    for (int t = 0; t < 2; ++t) {
+      const int g = g0 + t * kStep;
+      if (g >= g_hi) break;
+      uint16_t h[8], l[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) split_window(v[t][u], h[u], l[u]);
+      const uint32_t off = (uint32_t)g * (kRows * 16) + (uint32_t)row * 16;
+      *reinterpret_cast<uint4*>(hi + off) = pack8(h);
+      *reinterpret_cast<uint4*>(lo + off) = pack8(l);
+    }
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) apply_tc_kernel(const TcApplyParams P) {
+__global__ void __launch_bounds__(kThreads, 1)
+apply_tc_kernel(const TcApplyParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int Lp = P.Lp, L = P.L;
   const Smem S = smem_plan(Lp);
@@ -199,13 +257,21 @@ __global__ void __launch_bounds__(kThreads, 1) apply_tc_kernel(const TcApplyPara
   const uint32_t ncols = P.tmem_cols;
   const int nk = Lp / kKChunk;
   const int nhalf = Lp / 2;
-  const uint32_t idesc = idesc_bf16_f32(kRows, nhalf);
   const uint32_t sbase = smem_u32(smem);
 
   if (warp == 0) tmem_alloc(slot, ncols);
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+  if (tid == 32) {
+    for (int i = 0; i < 3; ++i) {
+      mbar_init(&bar[kQFull + i], 1);
+      mbar_init(&bar[kQEmpty + i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar[kWReady + i], kWorkers * 32);
+      mbar_init(&bar[kWFree + i], 1);
+    }
+    mbar_init(&bar[kDFull], 1);
+    mbar_init(&bar[kDEmpty], kWorkers * 32);
+    mbar_init(&bar[kStored], kWorkers * 32);
     fence_mbarrier_init();
     *abort_flag = 0;
   }
@@ -214,124 +280,146 @@ __global__ void __launch_bounds__(kThreads, 1) apply_tc_kernel(const TcApplyPara
   tc_fence_after();
   const uint32_t tmem = *slot;
 
-  uint32_t commits[2] = {0, 0}, waits[2] = {0, 0};
-  bool fresh = true;   // the window must be loaded whole (first block of a p-block)
-  for (int b = 0; b < P.nblk; ++b) {
-    const int c0 = P.c0[b];
-    if (fresh) load_window(smem, S, P, r0, c0, 0, Lp / 8);
-    const bool contig = b + 1 < P.nblk && P.c0[b + 1] == c0 + P.nb;
-    fence_async_smem();
-    __syncthreads();
-
-    // ---- the block's products, chunk by chunk ----------------------------------
-    const uint16_t* Qh = P.Qhi + (int64_t)b * Lp * Lp;
-    const uint16_t* Ql = P.Qlo + (int64_t)b * Lp * Lp;
-    auto stage = [&](int kc, int buf) {
-      // 16 k-rows of every column n of Q: two 16-byte pieces (k 0-7, 8-15) per n.
-      const uint32_t dst = sbase + S.q + (uint32_t)buf * 2 * S.q_part;
-      for (int e = tid; e < 2 * Lp; e += kThreads) {
-        const int nn = e >> 1, half = e & 1;
-        const uint32_t off = (uint32_t)half * (uint32_t)Lp * 16 + (uint32_t)nn * 16;
-        const int64_t src = (int64_t)nn * Lp + kc * kKChunk + half * 8;
-        cp_async16(dst + off, Qh + src);
-        cp_async16(dst + S.q_part + off, Ql + src);
-      }
-      cp_async_commit();
-    };
-    stage(0, 0);
-    for (int kc = 0; kc < nk; ++kc) {
-      const int buf = kc & 1;
-      if (kc + 1 < nk) {
-        const int nbuf = buf ^ 1;
-        if (commits[nbuf] > waits[nbuf]) {       // the MMAs of chunk kc-1 still read it
-          if (!mbar_wait_bounded(&bar[nbuf], waits[nbuf] & 1)) {
-            set_error(P.status, kDevTimeoutTma);
-            *abort_flag = 1;
-          }
-          ++waits[nbuf];
+  if (warp == 0) {
+    // ---- producer: Q chunks by TMA, three stages ahead -----------------------------
+    if (lane == 0) {
+      uint32_t cnt = 0;
+      for (int b = 0; b < P.nblk && !*abort_flag; ++b) {
+        for (int kc = 0; kc < nk; ++kc, ++cnt) {
+          const uint32_t st = cnt % kStages;
+          if (cnt >= (uint32_t)kStages &&
+              !wait_phase(&bar[kQEmpty + st], ((cnt / kStages) - 1) & 1, abort_flag, P.status))
+            break;
+          // The chunk is stored in global memory in exactly its shared-memory
+          // layout: one bulk copy each for hi and lo.
+          mbar_arrive_expect_tx(&bar[kQFull + st], S.q_stage);
+          unsigned char* dst = smem + S.q + st * S.q_stage;
+          const int64_t src = ((int64_t)b * nk + kc) * (S.q_part / 2);
+          bulk_g2s(dst, P.Qhi + src, S.q_part, &bar[kQFull + st]);
+          bulk_g2s(dst + S.q_part, P.Qlo + src, S.q_part, &bar[kQFull + st]);
         }
-        stage(kc + 1, nbuf);
-        cp_async_wait_1();
-      } else {
-        cp_async_wait_0();
       }
-      fence_async_smem();
-      __syncthreads();
-      if (*abort_flag) break;
-      if (tid == 0) {
+      // Leave no copy in flight: the last fill of each stage has landed.
+      for (uint32_t st = 0; st < (uint32_t)kStages && st < cnt; ++st) {
+        const uint32_t fills = (cnt - st + kStages - 1) / kStages;   // fills of stage st
+        (void)mbar_wait_bounded(&bar[kQFull + st], (fills - 1) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ------------------------------------------------------------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16_f32(kRows, nhalf);
+      uint32_t cnt = 0;
+      for (int b = 0; b < P.nblk; ++b) {
+        const int wb = b & 1;
+        if (!wait_phase(&bar[kWReady + wb], (b >> 1) & 1, abort_flag, P.status)) break;
+        if (b >= 1 && !wait_phase(&bar[kDEmpty], (b - 1) & 1, abort_flag, P.status)) break;
         tc_fence_after();
-        const uint32_t q0 = sbase + S.q + (uint32_t)buf * 2 * S.q_part;
-        const uint32_t a_off = (uint32_t)kc * 2 * (kRows * 16);
-        const uint64_t ah = smem_desc(sbase + S.w_hi + a_off, kRows * 16, kCoreBytes);
-        const uint64_t al = smem_desc(sbase + S.w_lo + a_off, kRows * 16, kCoreBytes);
+        const uint32_t wh = sbase + S.w + (uint32_t)wb * S.w_buf;
+        const uint32_t wl = wh + S.w_part;
+        bool ok = true;
+        for (int kc = 0; kc < nk; ++kc, ++cnt) {
+          const uint32_t st = cnt % kStages;
+          if (!wait_phase(&bar[kQFull + st], (cnt / kStages) & 1, abort_flag, P.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t q0 = sbase + S.q + st * S.q_stage;
+          const uint32_t a_off = (uint32_t)kc * 2 * (kRows * 16);
+          const uint64_t ah = smem_desc(wh + a_off, kRows * 16, kCoreBytes);
+          const uint64_t al = smem_desc(wl + a_off, kRows * 16, kCoreBytes);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t noff = (uint32_t)h * nhalf * 16;
-          const uint64_t bh = smem_desc(q0 + noff, (uint32_t)Lp * 16, kCoreBytes);
-          const uint64_t bl = smem_desc(q0 + S.q_part + noff, (uint32_t)Lp * 16, kCoreBytes);
-          const uint32_t d = tmem + (uint32_t)(h * nhalf);
-          tc_mma(d, ah, bh, idesc, kc > 0 ? 1u : 0u);
-          tc_mma(d, ah, bl, idesc, 1u);
-          tc_mma(d, al, bh, idesc, 1u);
+          for (int nh = 0; nh < 2; ++nh) {
+            const uint32_t noff = (uint32_t)nh * nhalf * 16;
+            const uint64_t bh = smem_desc(q0 + noff, (uint32_t)Lp * 16, kCoreBytes);
+            const uint64_t bl = smem_desc(q0 + S.q_part + noff, (uint32_t)Lp * 16, kCoreBytes);
+            const uint32_t d = tmem + (uint32_t)(nh * nhalf);
+            tc_mma(d, ah, bh, idesc, kc > 0 ? 1u : 0u);
+            tc_mma(d, ah, bl, idesc, 1u);
+            tc_mma(d, al, bh, idesc, 1u);
+          }
+          tc_commit(&bar[kQEmpty + st]);
         }
-        tc_commit(&bar[buf]);
-      }
-      ++commits[buf];
-    }
-    // ---- wait for every MMA of the block -----------------------------------------
-    for (int i = 0; i < 2; ++i) {
-      while (commits[i] > waits[i]) {
-        if (!mbar_wait_bounded(&bar[i], waits[i] & 1)) {
-          set_error(P.status, kDevTimeoutTma);
-          *abort_flag = 1;
-        }
-        ++waits[i];
+        if (!ok) break;
+        tc_commit(&bar[kDFull]);
+        tc_commit(&bar[kWFree + wb]);
       }
     }
-    __syncthreads();
-    if (*abort_flag) break;
-    tc_fence_after();
-
-    // ---- epilogue: finished columns to A, shared columns to the next window ------
-    {
-      const int q = warp & 3;                  // TMEM sub-partition = rows 32q .. 32q+31
-      const int row = 32 * q + lane;
-      const int grow = r0 + row;
-      const bool rok = grow < P.m;
-      const int per = Lp / 4;                  // columns per warp of the sub-partition
-      const int cbeg = (warp >> 2) * per;
+  } else {
+    // ---- workers: window loads and the epilogue ------------------------------------------
+    const int wt = tid - 64;
+    const int sp = warp & 3;                   // TMEM sub-partition this warp may read
+    const int cq = (warp - 2) >> 2;            // which quarter of the columns
+    const int per = Lp / 4;
+    const int row = 16 * sp + lane;            // M = 64: row r sits in lane (r/16)*32 + r%16
+    const bool rvalid = lane < 16 && r0 + row < P.m;
+    load_window(smem, S, P, 0, wt, r0, P.c0[0], 0, Lp / 8);
+    // Columns [L, Lp) of the second buffer are only ever padding; a window
+    // continued from the previous block never writes them, so zero them once
+    // (Q's padding rows are zero, but 0 * NaN is not).
+    for (int e = wt; e < (Lp - L) / 8 * kRows; e += kWorkers * 32) {
+      const uint32_t off = (uint32_t)(L / 8 + e / kRows) * (kRows * 16) + (uint32_t)(e % kRows) * 16;
+      unsigned char* w1 = smem + S.w + S.w_buf;
+      *reinterpret_cast<uint4*>(w1 + off) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(w1 + S.w_part + off) = make_uint4(0, 0, 0, 0);
+    }
+    fence_async_smem();
+    mbar_arrive(&bar[kWReady + 0]);
+    uint32_t fresh_loads = 0;
+    for (int b = 0; b < P.nblk; ++b) {
+      const int c0 = P.c0[b];
+      const bool has_next = b + 1 < P.nblk;
+      const bool contig = has_next && P.c0[b + 1] == c0 + P.nb;
+      const int ib = (b + 1) & 1;
+      if (contig) {
+        // The next window's new columns [kb, L), into the other buffer once
+        // the MMAs of block b-1 (its previous user) are done.
+        if (b >= 1 && !wait_phase(&bar[kWFree + ib], ((b - 1) >> 1) & 1, abort_flag, P.status)) break;
+        load_window(smem, S, P, ib, wt, r0, P.c0[b + 1], (L - P.nb) / 8, L / 8);
+      }
+      if (!wait_phase(&bar[kDFull], b & 1, abort_flag, P.status)) break;
+      tc_fence_after();
       const int keep = contig ? P.nb : L;      // columns at or past `keep` carry over
-      for (int j0 = cbeg; j0 < cbeg + per; j0 += 8) {
+      unsigned char* nhi = smem + S.w + (uint32_t)ib * S.w_buf;
+      for (int j0 = cq * per; j0 < (cq + 1) * per; j0 += 8) {
         float v[8];
-        tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)j0, v);
-        if (j0 >= L) continue;                 // padding columns
+        __syncwarp();
+        tmem_ld8(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)j0, v);
+        if (j0 >= L || !(lane < 16)) continue;
         if (j0 >= keep) {
           uint16_t h[8], l[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) split_f32(v[u], h[u], l[u]);
-          put_window8(smem, S, row, (j0 - P.nb) / 8, pack8(h), pack8(l));
-        } else if (rok) {
+          const uint32_t off = (uint32_t)((j0 - P.nb) / 8) * (kRows * 16) + (uint32_t)row * 16;
+          *reinterpret_cast<uint4*>(nhi + off) = pack8(h);
+          *reinterpret_cast<uint4*>(nhi + S.w_part + off) = pack8(l);
+        } else if (rvalid) {
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const int col = j0 + u;
-            const int gc = c0 + col;
-            if (col < keep && gc >= 0 && gc < P.n) __stcg(P.A + (int64_t)gc * P.lda + grow, (double)v[u]);
+            const int gc = c0 + j0 + u;
+            if (gc >= 0 && gc < P.n) __stcg(P.A + (int64_t)gc * P.lda + r0 + row, f32_to_f64(v[u]));
           }
         }
       }
+      tc_fence_before();
+      mbar_arrive(&bar[kDEmpty]);
+      if (has_next && !contig) {
+        // A new p-block: its first window overlaps columns just stored, so
+        // every worker's stores come first.
+        __threadfence_block();
+        mbar_arrive(&bar[kStored]);
+        if (!wait_phase(&bar[kStored], fresh_loads & 1, abort_flag, P.status)) break;
+        ++fresh_loads;
+        load_window(smem, S, P, ib, wt, r0, P.c0[b + 1], 0, Lp / 8);
+      }
+      if (has_next) {
+        fence_async_smem();
+        mbar_arrive(&bar[kWReady + ib]);
+      }
     }
-    tc_fence_before();
-    __syncthreads();   // the shared columns are in place; TMEM may be overwritten
-    if (contig) {
-      // The next window's columns [kb, L) are new: read them from A.
-      load_window(smem, S, P, r0, P.c0[b + 1], (L - P.nb) / 8, L / 8);
-    }
-    fresh = !contig;
   }
-  cp_async_wait_0();
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
+    __syncwarp();
     tc_fence_after();
     tmem_dealloc(tmem, ncols);
   }
@@ -342,10 +430,12 @@ __global__ void __launch_bounds__(kThreads, 1) apply_tc_kernel(const TcApplyPara
 size_t apply_tc_smem_bytes(int Lp) { return smem_plan(Lp).total; }
 
 bool apply_tc_supported(int L, int Lp, int nb) {
-  // N = Lp/2 per MMA (a multiple of 16, at most 256); the window, two staged
-  // chunks and the barriers fit in shared memory; nb and L - nb are whole
-  // 8-column groups (the carried columns move in 16-byte pieces).
-  return Lp % 32 == 0 && Lp <= 512 && nb % 8 == 0 && L % 8 == 0 && apply_tc_smem_bytes(Lp) <= 227 * 1024;
+  // N = Lp/2 per MMA (a multiple of 16, at most 256; one TMA box of Lp/2 rows);
+  // two windows, three chunk stages and the barriers fit in shared memory; nb
+  // and L - nb are whole 8-column groups (the carried columns move in 16-byte
+  // pieces).
+  return Lp % 32 == 0 && Lp <= 512 && nb % 8 == 0 && L % 8 == 0 && L <= Lp &&
+         apply_tc_smem_bytes(Lp) <= 227 * 1024;
 }
 
 cudaError_t launch_apply_tc(const TcApplyParams& P, cudaStream_t s) {
@@ -355,6 +445,35 @@ cudaError_t launch_apply_tc(const TcApplyParams& P, cudaStream_t s) {
   const unsigned grid = (unsigned)((P.m + kRows - 1) / kRows);
   apply_tc_kernel<<<grid, kThreads, smem, s>>>(P);
   return cudaGetLastError();
+}
+
+// Q (nblk blocks of Lp x Lp FP64, column n holding k contiguous) split into
+// BF16 hi/lo, written in the order the apply kernel stages it: for block b,
+// chunk kc of 16 k, k-group kg of 8 k, column n, the 8 values k = 16kc+8kg ..
+// +7 form one 16-byte piece at (((b*nk + kc)*2 + kg)*Lp + n)*8.
+__global__ void split_chunked_kernel(const double* __restrict__ Q, uint16_t* __restrict__ hi,
+                                     uint16_t* __restrict__ lo, int Lp, long long total) {
+  const int nk = Lp / kKChunk;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int kk = (int)(e & 7);
+    const long long r = e >> 3;
+    const int n = (int)(r % Lp);
+    const long long r2 = r / Lp;
+    const int kg = (int)(r2 & 1);
+    const long long r3 = r2 >> 1;
+    const int kc = (int)(r3 % nk);
+    const long long b = r3 / nk;
+    const double q = Q[(b * Lp + n) * Lp + kc * kKChunk + kg * 8 + kk];
+    uint16_t h, l;
+    split_f64(q, h, l);
+    hi[e] = h;
+    lo[e] = l;
+  }
+}
+
+void split_chunked(const double* Q, uint16_t* hi, uint16_t* lo, int Lp, long long nblk, cudaStream_t s) {
+  split_chunked_kernel<<<1024, 256, 0, s>>>(Q, hi, lo, Lp, nblk * Lp * Lp);
 }
 
 }  // namespace rs

@@ -16,7 +16,7 @@ struct TcApplyParams {
   int nb;                 // columns a window advances within a p-block
   int nblk;
   const int* c0;          // first window column of each block, in apply order
-  const uint16_t* Qhi;    // nblk x Lp x Lp BF16, column n holds k contiguous
+  const uint16_t* Qhi;    // nblk x Lp x Lp BF16 in the staging order of split_chunked
   const uint16_t* Qlo;
   uint32_t tmem_cols;     // power of two >= Lp (the accumulator's columns)
   int* status;            // first device error (timeouts), 0 if none
@@ -26,5 +26,9 @@ struct TcApplyParams {
 bool apply_tc_supported(int L, int Lp, int nb);
 size_t apply_tc_smem_bytes(int Lp);
 cudaError_t launch_apply_tc(const TcApplyParams& P, cudaStream_t s);
+
+// Split Q (nblk blocks of Lp x Lp FP64, column-major) into the BF16 hi/lo
+// operands of launch_apply_tc, in its staging order.
+void split_chunked(const double* Q, uint16_t* hi, uint16_t* lo, int Lp, long long nblk, cudaStream_t s);
 
 }  // namespace rs

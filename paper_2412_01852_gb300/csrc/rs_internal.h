@@ -41,6 +41,9 @@ bool encode_tile_map_2d(CUtensorMap* map, const void* base, bool is_double, uint
                         uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
                         uint32_t box_outer);
 
+bool encode_tile_map_2d_b16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
+                            uint64_t row_pitch_bytes, uint32_t box_inner, uint32_t box_outer);
+
 // Record a failed CUDA call for rot_last_error(); returns ROT_ECUDA.
 rot_status cuda_failed(cudaError_t e, const char* where);
 void note_error(const char* what);

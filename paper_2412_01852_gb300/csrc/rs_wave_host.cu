@@ -63,6 +63,21 @@ bool encode_tile_map_2d(CUtensorMap* map, const void* base, bool is_double, uint
   return r == CUDA_SUCCESS;
 }
 
+// The same for 16-bit elements (the tensor-core block apply's BF16 operands).
+bool encode_tile_map_2d_b16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
+                            uint64_t row_pitch_bytes, uint32_t box_inner, uint32_t box_outer) {
+  auto fn = get_encode();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {row_pitch_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // ---- planning -------------------------------------------------------------------
 static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 static inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
