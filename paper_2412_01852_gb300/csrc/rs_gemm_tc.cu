@@ -119,56 +119,40 @@ __device__ __forceinline__ void split_f64(double x, uint16_t& h, uint16_t& l) {
   h = __bfloat16_as_ushort(hb);
   l = __bfloat16_as_ushort(lb);
 }
-__device__ __forceinline__ void split_f32(float x, uint16_t& h, uint16_t& l) {
-  const __nv_bfloat16 hb = __float2bfloat16_rn(x);
-  const __nv_bfloat16 lb = __float2bfloat16_rn(x - __bfloat162float(hb));  // exact difference
-  h = __bfloat16_as_ushort(hb);
-  l = __bfloat16_as_ushort(lb);
-}
 // FP64 <-> FP32 by integer bit operations.  GB300's FP64 pipe (2 lanes per
 // clock per SM) would otherwise be this kernel's bottleneck: a conversion
 // instruction there costs as much as a DFMA.
 // FP64 -> FP32 rounding toward zero (relative error below 2^-23, far below the
-// split's 2^-17); magnitudes outside FP32's normal range go to 0 or Inf.
+// split's 2^-17): rebias the exponent in the high word, then one funnel shift
+// moves exponent and mantissa into place.  Magnitudes below FP32's normal
+// range become zero; above it Inf; NaN stays NaN.
 __device__ __forceinline__ float f64_to_f32_rz(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
-  const uint32_t sign = hi & 0x80000000u;
-  const uint32_t ed = (hi >> 20) & 0x7ffu;
-  const int e = (int)ed - 1023 + 127;
-  const uint32_t mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  uint32_t f;
-  if (ed == 0x7ffu) f = sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u);   // Inf, NaN
-  else if (e <= 0) f = sign;
-  else if (e >= 255) f = sign | 0x7f800000u;
-  else f = sign | ((uint32_t)e << 23) | mant;
-  return __uint_as_float(f);
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t ax = hi & 0x7fffffffu;
+  const int32_t t = (int32_t)(ax - (896u << 20));          // exponent - (1023 - 127)
+  uint32_t f = __funnelshift_l(lo, (uint32_t)t, 3);
+  if (t <= 0) f = 0u;
+  if (t >= (int32_t)(255u << 20)) f = (ax > 0x7ff00000u || (ax == 0x7ff00000u && lo)) ? 0x7fc00000u : 0x7f800000u;
+  return __uint_as_float(f | (hi & 0x80000000u));
 }
 // FP32 -> FP64, exact for zeros, normal numbers, Inf and NaN (FP32 subnormals
 // become signed zero).
 __device__ __forceinline__ double f32_to_f64(float v) {
   const uint32_t u = __float_as_uint(v);
-  const uint32_t sign = u & 0x80000000u;
-  const uint32_t e = (u >> 23) & 0xffu;
-  const uint32_t m = u & 0x7fffffu;
-  uint32_t hi, lo = m << 29;
-  if (e == 0) { hi = sign; lo = 0; }
-  else if (e == 255) hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
-  else hi = sign | ((e + (1023u - 127u)) << 20) | (m >> 3);
-  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+  const uint32_t au = u & 0x7fffffffu;
+  uint32_t dhi = (au >> 3) + (896u << 20), dlo = u << 29;
+  if (au < 0x00800000u) dhi = dlo = 0u;
+  if (au >= 0x7f800000u) dhi = 0x7ff00000u | (au >> 3);
+  return __hiloint2double((int)(dhi | (u & 0x80000000u)), (int)dlo);
 }
-// The window's split: x -> FP32 (by bits), then hi/lo in FP32.
-__device__ __forceinline__ void split_window(double x, uint16_t& h, uint16_t& l) {
-  split_f32(f64_to_f32_rz(x), h, l);
-}
-
-__device__ __forceinline__ uint4 pack8(const uint16_t (&e)[8]) {
-  uint4 u;
-  u.x = (uint32_t)e[0] | ((uint32_t)e[1] << 16);
-  u.y = (uint32_t)e[2] | ((uint32_t)e[3] << 16);
-  u.z = (uint32_t)e[4] | ((uint32_t)e[5] << 16);
-  u.w = (uint32_t)e[6] | ((uint32_t)e[7] << 16);
-  return u;
+// Two FP32 values -> their BF16 hi parts and BF16 lo parts (x = hi + lo + r,
+// |r| <= 2^-17 |x|), each pair packed low-first.
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  const float ha = __uint_as_float(hi << 16), hb = __uint_as_float(hi & 0xffff0000u);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - ha, b - hb);   // exact differences
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // Shared-memory plan (byte offsets from the dynamic base, Lp = padded width):
@@ -208,20 +192,23 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volat
 
 // Window columns [g_lo*8, g_hi*8) of the block whose window starts at global
 // column c0: FP64 from A, split, into buffer `wbuf`.  Columns outside [0, n),
-// at or past L, and rows outside [0, m) are zero.  `wt` is the worker thread.
+// at or past L, and rows outside [0, m) are zero.  `wt` is the worker thread;
+// each handles one row and up to kGroupsInFlight 8-column groups at a time,
+// all of whose loads are issued before the first is used.
+constexpr int kGroupsInFlight = 4;
 __device__ void load_window(unsigned char* smem, const Smem& S, const TcApplyParams& P, int wbuf, int wt, int r0,
                             int c0, int g_lo, int g_hi) {
   const int row = wt % kRows;
   const int grow = r0 + row;
   const bool rok = grow < P.m;
-  const double* arow = P.A + grow;
+  const double* arow = P.A + (rok ? grow : 0);
   unsigned char* hi = smem + S.w + (uint32_t)wbuf * S.w_buf;
   unsigned char* lo = hi + S.w_part;
-  constexpr int kStep = kWorkers * 32 / kRows;   // 8-column groups handled per pass
-  for (int g0 = g_lo + wt / kRows; g0 < g_hi; g0 += 2 * kStep) {
-    double v[2][8];
+  constexpr int kStep = kWorkers * 32 / kRows;   // threads per row
+  for (int g0 = g_lo + wt / kRows; g0 < g_hi; g0 += kGroupsInFlight * kStep) {
+    double v[kGroupsInFlight][8];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < kGroupsInFlight; ++t) {
       const int g = g0 + t * kStep;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -231,15 +218,17 @@ __device__ void load_window(unsigned char* smem, const Smem& S, const TcApplyPar
       }
     }
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < kGroupsInFlight; ++t) {
       const int g = g0 + t * kStep;
       if (g >= g_hi) break;
-      uint16_t h[8], l[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) split_window(v[t][u], h[u], l[u]);
+      uint4 h, l;
+      split_pair(f64_to_f32_rz(v[t][0]), f64_to_f32_rz(v[t][1]), h.x, l.x);
+      split_pair(f64_to_f32_rz(v[t][2]), f64_to_f32_rz(v[t][3]), h.y, l.y);
+      split_pair(f64_to_f32_rz(v[t][4]), f64_to_f32_rz(v[t][5]), h.z, l.z);
+      split_pair(f64_to_f32_rz(v[t][6]), f64_to_f32_rz(v[t][7]), h.w, l.w);
       const uint32_t off = (uint32_t)g * (kRows * 16) + (uint32_t)row * 16;
-      *reinterpret_cast<uint4*>(hi + off) = pack8(h);
-      *reinterpret_cast<uint4*>(lo + off) = pack8(l);
+      *reinterpret_cast<uint4*>(hi + off) = h;
+      *reinterpret_cast<uint4*>(lo + off) = l;
     }
   }
 }
@@ -349,8 +338,7 @@ apply_tc_kernel(const TcApplyParams P) {
     const int sp = warp & 3;                   // TMEM sub-partition this warp may read
     const int cq = (warp - 2) >> 2;            // which quarter of the columns
     const int per = Lp / 4;
-    const int row = 16 * sp + lane;            // M = 64: row r sits in lane (r/16)*32 + r%16
-    const bool rvalid = lane < 16 && r0 + row < P.m;
+    // M = 64: accumulator row r sits in TMEM lane (r/16)*32 + r%16.
     load_window(smem, S, P, 0, wt, r0, P.c0[0], 0, Lp / 8);
     // Columns [L, Lp) of the second buffer are only ever padding; a window
     // continued from the previous block never writes them, so zero them once
@@ -379,23 +367,36 @@ apply_tc_kernel(const TcApplyParams P) {
       tc_fence_after();
       const int keep = contig ? P.nb : L;      // columns at or past `keep` carry over
       unsigned char* nhi = smem + S.w + (uint32_t)ib * S.w_buf;
+      // Lanes 0-15 of the warp hold rows 16sp .. 16sp+15 (M = 64); each
+      // 8-column piece is shared with lanes 16-31, which take its upper half.
+      const int half = lane >> 4;
+      const int prow = 16 * sp + (lane & 15);
+      const bool pvalid = r0 + prow < P.m;
       for (int j0 = cq * per; j0 < (cq + 1) * per; j0 += 8) {
         float v[8];
         __syncwarp();
         tmem_ld8(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)j0, v);
-        if (j0 >= L || !(lane < 16)) continue;
+        float w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = __shfl_sync(0xffffffffu, v[4 + u], lane & 15);
+        if (half) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = w[u];
+        }
+        if (j0 >= L) continue;                   // padding columns
+        const int jc = j0 + 4 * half;            // this lane's first column
         if (j0 >= keep) {
-          uint16_t h[8], l[8];
+          uint2 h, l;
+          split_pair(v[0], v[1], h.x, l.x);
+          split_pair(v[2], v[3], h.y, l.y);
+          const uint32_t off = (uint32_t)((j0 - P.nb) / 8) * (kRows * 16) + (uint32_t)prow * 16 + 8 * half;
+          *reinterpret_cast<uint2*>(nhi + off) = h;
+          *reinterpret_cast<uint2*>(nhi + S.w_part + off) = l;
+        } else if (pvalid) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) split_f32(v[u], h[u], l[u]);
-          const uint32_t off = (uint32_t)((j0 - P.nb) / 8) * (kRows * 16) + (uint32_t)row * 16;
-          *reinterpret_cast<uint4*>(nhi + off) = pack8(h);
-          *reinterpret_cast<uint4*>(nhi + S.w_part + off) = pack8(l);
-        } else if (rvalid) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int gc = c0 + j0 + u;
-            if (gc >= 0 && gc < P.n) __stcg(P.A + (int64_t)gc * P.lda + r0 + row, f32_to_f64(v[u]));
+          for (int u = 0; u < 4; ++u) {
+            const int gc = c0 + jc + u;
+            if (gc >= 0 && gc < P.n) __stcg(P.A + (int64_t)gc * P.lda + r0 + prow, f32_to_f64(v[u]));
           }
         }
       }
