@@ -120,15 +120,24 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
     // no wave window and no j restriction (plain problems only).
     const bool interior = (wend - ws == U) && kr == KMAX && ws >= KMAX - 1 && ws + U + 1 <= n - 1;
     if (interior) {
+      // Column pointers advance by one column per wave (no per-access
+      // multiply).  Whether the next tile's columns all exist is decided
+      // once for the tile: if it is not whole, only its first column (the
+      // one an edge tile takes from `pre`) is fetched.
+      const bool next_whole = ws + 2 * U <= col_hi;
+      const bool next_first = ws + U + 1 <= col_hi;
+      const T* pl = reinterpret_cast<const T*>(I.A) + (int64_t)(ws + U + 1) * lda + c * (32 * R) + lane;
+      T* ps = reinterpret_cast<T*>(I.A) + (int64_t)(ws + 1 - KMAX) * lda + c * (32 * R) + lane;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int w = ws + u;
-        const int qn = w + U + 1;            // this slot's column in the next tile
+        const bool fetch = u == 0 ? next_first : next_whole;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           win[r][(KMAX + u) % U] = pre[r][u];
-          pre[r][u] = (rowok[r] && qn <= col_hi) ? ld_cg(arow[r] + (int64_t)qn * lda) : T(0);
+          pre[r][u] = T(0);
+          if (fetch && rowok[r]) pre[r][u] = ld_cg(pl + r * 32);
         }
+        pl += lda;
         const V2* trow = tl + u * KMAX;
 #pragma unroll
         for (int l = 0; l < KMAX; ++l) {
@@ -137,10 +146,11 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
           for (int r = 0; r < R; ++r)
             rotate(win[r][(KMAX - 1 - l + u) % U], win[r][(KMAX - l + u) % U], cs.x, cs.y);
         }
-        const int q = w + 1 - KMAX;          // >= own_lo and >= 0 in an interior tile
+        // column w + 1 - KMAX (>= own_lo and >= 0 in an interior tile) retires
 #pragma unroll
         for (int r = 0; r < R; ++r)
-          if (rowok[r]) st_cg(arow[r] + (int64_t)q * lda, win[r][u % U]);
+          if (rowok[r]) st_cg(ps + r * 32, win[r][u % U]);
+        ps += lda;
       }
     } else {
       T nextcol[R];

@@ -206,10 +206,11 @@ rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const 
 }
 
 // FP32: 64-row chains (2 rows per lane), p-blocks of 8 sequences, 9-wave
-// tiles, 4 tiles per item, 2 CTAs of 8 warps per SM.  Measured on GB300
-// (A 8192x8192, k = 192): this shape 3.72 ms; 16-sequence p-blocks with
-// 17-wave tiles 4.88 ms (their unrolled tile no longer fits the instruction
-// cache); 12-sequence 3.91 ms; 4 rows per lane 4.04 ms.
+// tiles, 6 tiles per item, 2 CTAs of 8 warps per SM.  Measured on GB300
+// (A 8192x8192, k = 192): this shape 3.43 ms (4 tiles per item 3.53, 8 tiles
+// 3.56); 16-sequence p-blocks with 17-wave tiles 4.51 ms (their unrolled tile
+// strains the instruction cache); 12-sequence 3.70 ms; 4 rows per lane
+// 3.88 ms.
 static constexpr int kF32Kmax = 8;
 static constexpr int kF32R = 2;
 static constexpr int kF32NBT = kF32Kmax + 1;
@@ -240,7 +241,7 @@ static cudaError_t launch_wave_f32(const WaveProblem& P, const CUtensorMap& map,
 
 rot_status wave_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C,
                           int64_t ldc, const float* S, int64_t lds, cudaStream_t stream, const WaveOptions& opt) {
-  const WavePlan pl = plan_wave(m, n, k, kF32Kmax, kF32NBT, opt.K, opt.NB > 0 ? opt.NB : 4 * kF32NBT, 4,
+  const WavePlan pl = plan_wave(m, n, k, kF32Kmax, kF32NBT, opt.K, opt.NB > 0 ? opt.NB : 6 * kF32NBT, 4,
                                 32 * kF32R);
   const int64_t W2 = 2 * (int64_t)pl.kpad;
   const size_t cs_bytes = (size_t)pl.cs_rows * W2 * sizeof(float);
