@@ -345,6 +345,7 @@ def main():
                                         "%.3f GHz max SM clock" % (props.multi_processor_count,
                                                                    FP64_FMA_PER_SM_CLK, max_clk_ghz),
                          "dfma_probe_tflops": peak_gflops / 1e3,
+                         "frac_of_dfma_probe": achieved_tflops / (peak_gflops / 1e3) if peak_gflops else None,
                          "rotation_ceiling_frac": 0.75},
             "cpu_baseline": cpu,
             "e2e": e2e,
