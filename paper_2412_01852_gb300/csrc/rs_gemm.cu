@@ -11,10 +11,10 @@
 // the identity start as unit vectors, which lets whole waves on zero columns
 // be skipped (values are unchanged; only the sign of zeros can differ).
 //
-// Block apply: split BF16 runs on the 5th-generation tensor cores (tcgen05,
-// TMEM accumulator; rs_gemm_tc.cu) for windows up to 320 columns.  The other
-// modes, and wider windows, use mma.sync: one CTA per 32-row tile of A walks
-// the blocks in order.  Modes:
+// Block apply: the split modes run on the 5th-generation tensor cores
+// (tcgen05, TMEM accumulators; rs_gemm_tc.cu) for windows up to 320 columns.
+// FP64 DMMA, and wider windows, use mma.sync: one CTA per 32-row tile of A
+// walks the blocks in order.  Modes:
 //   ROT_GEMM_F64_DMMA   FP64 tensor MMA (m8n8k4), FP64 accumulation;
 //   ROT_GEMM_SPLIT_BF16 x = hi + lo in BF16; hi*hi + hi*lo + lo*hi in FP32;
 //   ROT_GEMM_SPLIT_F16  x = hi + lo*2^-11 in FP16; hi*hi in one FP32
@@ -700,31 +700,29 @@ rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t ld
     const long long qe = (long long)nblk * Lp * Lp;
     cudaError_t e = cudaSuccess;
     const int tr = rs::trace_begin(ROT_KERNEL_GEMM_APPLY, m * (n - 1) * k, s);
-    if (mode == ROT_GEMM_SPLIT_BF16) {
-      if (rs::apply_tc_supported(L, Lp, nb)) {
-        rs::split_chunked(Q, const_cast<uint16_t*>(P.Qhi), const_cast<uint16_t*>(P.Qlo), Lp, nblk, s);
-        // tcgen05: 128-row tiles, accumulator in tensor memory.
-        rs::TcApplyParams T{};
-        T.A = A; T.lda = lda; T.m = (int)m; T.n = (int)n; T.L = L; T.Lp = Lp; T.nb = nb;
-        T.nblk = (int)nblk;
-        T.c0 = P.c0;
-        T.Qhi = P.Qhi;
-        T.Qlo = P.Qlo;
-        uint32_t cols = 32;
-        while (cols < (uint32_t)Lp) cols <<= 1;
-        T.tmem_cols = cols;
-        T.status = reinterpret_cast<int*>(base + o_status);
-        e = cudaMemsetAsync(T.status, 0, sizeof(int), s);
-        if (e == cudaSuccess) e = rs::launch_apply_tc(T, s);
-        if (e == cudaSuccess) {
-          rs::record_status_async(T.status, s);
-          rs::count_launches(1);
-        }
-      } else {
-        rs::split_kernel<ROT_GEMM_SPLIT_BF16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
-                                                                    const_cast<uint16_t*>(P.Qlo), qe);
-        e = rs::launch_apply<ROT_GEMM_SPLIT_BF16>(P, s);
+    if (mode != ROT_GEMM_F64_DMMA && rs::apply_tc_supported(L, Lp, nb)) {
+      // tcgen05: 64-row tiles, accumulator in tensor memory.
+      rs::split_chunked(Q, const_cast<uint16_t*>(P.Qhi), const_cast<uint16_t*>(P.Qlo), Lp, nblk, mode, s);
+      rs::TcApplyParams T{};
+      T.A = A; T.lda = lda; T.m = (int)m; T.n = (int)n; T.L = L; T.Lp = Lp; T.nb = nb;
+      T.nblk = (int)nblk;
+      T.c0 = P.c0;
+      T.Qhi = P.Qhi;
+      T.Qlo = P.Qlo;
+      uint32_t cols = 32;
+      while (cols < (uint32_t)Lp) cols <<= 1;
+      T.tmem_cols = cols;
+      T.status = reinterpret_cast<int*>(base + o_status);
+      e = cudaMemsetAsync(T.status, 0, sizeof(int), s);
+      if (e == cudaSuccess) e = rs::launch_apply_tc(T, mode, s);
+      if (e == cudaSuccess) {
+        rs::record_status_async(T.status, s);
+        rs::count_launches(1);
       }
+    } else if (mode == ROT_GEMM_SPLIT_BF16) {
+      rs::split_kernel<ROT_GEMM_SPLIT_BF16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
+                                                                  const_cast<uint16_t*>(P.Qlo), qe);
+      e = rs::launch_apply<ROT_GEMM_SPLIT_BF16>(P, s);
     } else if (mode == ROT_GEMM_SPLIT_F16) {
       rs::split_kernel<ROT_GEMM_SPLIT_F16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
                                                                  const_cast<uint16_t*>(P.Qlo), qe);

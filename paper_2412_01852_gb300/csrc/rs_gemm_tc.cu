@@ -6,6 +6,10 @@
 // lo = bf16(x - hi), and A_win * Q_b is formed as
 //     A_hi*Q_hi + A_hi*Q_lo + A_lo*Q_hi
 // in one FP32 accumulator (the lo*lo term, ~2^-16 relative, is dropped).
+// Split FP16: x = hi + 2^-11 lo with lo = fp16((x - hi) * 2^11) kept in
+// FP16's normal range; hi*hi and hi*lo + lo*hi go to two accumulators,
+// combined as acc0 + 2^-11 acc1.  Both accumulators of all Lp columns do not
+// fit in TMEM, so each block runs as two passes of Lp/2 output columns.
 //
 // One CTA owns a tile of 64 rows of A (M = 64) and walks the blocks in their
 // order with three roles:
@@ -30,6 +34,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "rs_device.cuh"
 #include "rs_gemm_tc.h"
@@ -59,10 +64,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 }
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5
-// = 1), A and B BF16 (bits 7-9 and 10-12 = 1), both K-major, N/8 at bits
-// 17-22, M/16 at bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// = 1), A and B BF16 (bits 7-9 and 10-12 = 1) or FP16 (0), both K-major, N/8
+// at bits 17-22, M/16 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_f32acc(bool bf16, int M, int N) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 // ---- tcgen05 wrappers ----------------------------------------------------------
@@ -145,14 +151,25 @@ __device__ __forceinline__ double f32_to_f64(float v) {
   if (au >= 0x7f800000u) dhi = 0x7ff00000u | (au >> 3);
   return __hiloint2double((int)(dhi | (u & 0x80000000u)), (int)dlo);
 }
-// Two FP32 values -> their BF16 hi parts and BF16 lo parts (x = hi + lo + r,
-// |r| <= 2^-17 |x|), each pair packed low-first.
+// Two FP32 values -> their hi parts and lo parts, each pair packed low-first.
+//   BF16:  x = hi + lo + r,           |r| <= 2^-17 |x|
+//   FP16:  x = hi + 2^-11 lo + r,     lo = RN16((x - hi) * 2^11), |r| <= 2^-22 |x|
+//          (lo is kept scaled so that it stays in FP16's normal range).
+template <int MODE>
 __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  const float ha = __uint_as_float(hi << 16), hb = __uint_as_float(hi & 0xffff0000u);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(a - ha, b - hb);   // exact differences
-  lo = *reinterpret_cast<const uint32_t*>(&l);
+  if constexpr (MODE == ROT_GEMM_SPLIT_BF16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    const float ha = __uint_as_float(hi << 16), hb = __uint_as_float(hi & 0xffff0000u);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - ha, b - hb);   // exact differences
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+  } else {
+    const __half2 h = __floats2half2_rn(a, b);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn((a - hf.x) * 2048.f, (b - hf.y) * 2048.f);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+  }
 }
 
 // Shared-memory plan (byte offsets from the dynamic base, Lp = padded width):
@@ -196,6 +213,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volat
 // each handles one row and up to kGroupsInFlight 8-column groups at a time,
 // all of whose loads are issued before the first is used.
 constexpr int kGroupsInFlight = 4;
+template <int MODE>
 __device__ void load_window(unsigned char* smem, const Smem& S, const TcApplyParams& P, int wbuf, int wt, int r0,
                             int c0, int g_lo, int g_hi) {
   const int row = wt % kRows;
@@ -222,10 +240,10 @@ __device__ void load_window(unsigned char* smem, const Smem& S, const TcApplyPar
       const int g = g0 + t * kStep;
       if (g >= g_hi) break;
       uint4 h, l;
-      split_pair(f64_to_f32_rz(v[t][0]), f64_to_f32_rz(v[t][1]), h.x, l.x);
-      split_pair(f64_to_f32_rz(v[t][2]), f64_to_f32_rz(v[t][3]), h.y, l.y);
-      split_pair(f64_to_f32_rz(v[t][4]), f64_to_f32_rz(v[t][5]), h.z, l.z);
-      split_pair(f64_to_f32_rz(v[t][6]), f64_to_f32_rz(v[t][7]), h.w, l.w);
+      split_pair<MODE>(f64_to_f32_rz(v[t][0]), f64_to_f32_rz(v[t][1]), h.x, l.x);
+      split_pair<MODE>(f64_to_f32_rz(v[t][2]), f64_to_f32_rz(v[t][3]), h.y, l.y);
+      split_pair<MODE>(f64_to_f32_rz(v[t][4]), f64_to_f32_rz(v[t][5]), h.z, l.z);
+      split_pair<MODE>(f64_to_f32_rz(v[t][6]), f64_to_f32_rz(v[t][7]), h.w, l.w);
       const uint32_t off = (uint32_t)g * (kRows * 16) + (uint32_t)row * 16;
       *reinterpret_cast<uint4*>(hi + off) = h;
       *reinterpret_cast<uint4*>(lo + off) = l;
@@ -233,8 +251,14 @@ __device__ void load_window(unsigned char* smem, const Smem& S, const TcApplyPar
   }
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 apply_tc_kernel(const TcApplyParams P) {
+  // Split BF16: one pass per block over all Lp output columns (both halves
+  // of N per chunk), one accumulator.  Split FP16: one pass per half of the
+  // columns, each with two accumulators (hi*hi and the scaled cross terms).
+  constexpr bool kBF16 = MODE == ROT_GEMM_SPLIT_BF16;
+  constexpr int kPasses = kBF16 ? 1 : 2;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int Lp = P.Lp, L = P.L;
   const Smem S = smem_plan(Lp);
@@ -247,6 +271,8 @@ apply_tc_kernel(const TcApplyParams P) {
   const int nk = Lp / kKChunk;
   const int nhalf = Lp / 2;
   const uint32_t sbase = smem_u32(smem);
+  // bytes of one staged operand (hi or lo) of one chunk
+  const uint32_t part_bytes = kBF16 ? S.q_part : S.q_part / 2;
 
   if (warp == 0) tmem_alloc(slot, ncols);
   if (tid == 32) {
@@ -273,7 +299,7 @@ apply_tc_kernel(const TcApplyParams P) {
     // ---- producer: Q chunks by TMA, three stages ahead -----------------------------
     if (lane == 0) {
       uint32_t cnt = 0;
-      for (int b = 0; b < P.nblk && !*abort_flag; ++b) {
+      for (int t = 0; t < P.nblk * kPasses && !*abort_flag; ++t) {
         for (int kc = 0; kc < nk; ++kc, ++cnt) {
           const uint32_t st = cnt % kStages;
           if (cnt >= (uint32_t)kStages &&
@@ -281,11 +307,11 @@ apply_tc_kernel(const TcApplyParams P) {
             break;
           // The chunk is stored in global memory in exactly its shared-memory
           // layout: one bulk copy each for hi and lo.
-          mbar_arrive_expect_tx(&bar[kQFull + st], S.q_stage);
+          mbar_arrive_expect_tx(&bar[kQFull + st], 2 * part_bytes);
           unsigned char* dst = smem + S.q + st * S.q_stage;
-          const int64_t src = ((int64_t)b * nk + kc) * (S.q_part / 2);
-          bulk_g2s(dst, P.Qhi + src, S.q_part, &bar[kQFull + st]);
-          bulk_g2s(dst + S.q_part, P.Qlo + src, S.q_part, &bar[kQFull + st]);
+          const int64_t src = ((int64_t)t * nk + kc) * (part_bytes / 2);
+          bulk_g2s(dst, P.Qhi + src, part_bytes, &bar[kQFull + st]);
+          bulk_g2s(dst + S.q_part, P.Qlo + src, part_bytes, &bar[kQFull + st]);
         }
       }
       // Leave no copy in flight: the last fill of each stage has landed.
@@ -297,38 +323,51 @@ apply_tc_kernel(const TcApplyParams P) {
   } else if (warp == 1) {
     // ---- MMA issuer ------------------------------------------------------------------
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(kRows, nhalf);
+      const uint32_t idesc = idesc_f32acc(kBF16, kRows, nhalf);
       uint32_t cnt = 0;
-      for (int b = 0; b < P.nblk; ++b) {
+      bool ok = true;
+      for (int b = 0; b < P.nblk && ok; ++b) {
         const int wb = b & 1;
         if (!wait_phase(&bar[kWReady + wb], (b >> 1) & 1, abort_flag, P.status)) break;
-        if (b >= 1 && !wait_phase(&bar[kDEmpty], (b - 1) & 1, abort_flag, P.status)) break;
-        tc_fence_after();
         const uint32_t wh = sbase + S.w + (uint32_t)wb * S.w_buf;
         const uint32_t wl = wh + S.w_part;
-        bool ok = true;
-        for (int kc = 0; kc < nk; ++kc, ++cnt) {
-          const uint32_t st = cnt % kStages;
-          if (!wait_phase(&bar[kQFull + st], (cnt / kStages) & 1, abort_flag, P.status)) { ok = false; break; }
+        for (int h = 0; h < kPasses && ok; ++h) {
+          const int t = b * kPasses + h;
+          if (t >= 1 && !wait_phase(&bar[kDEmpty], (t - 1) & 1, abort_flag, P.status)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t q0 = sbase + S.q + st * S.q_stage;
-          const uint32_t a_off = (uint32_t)kc * 2 * (kRows * 16);
-          const uint64_t ah = smem_desc(wh + a_off, kRows * 16, kCoreBytes);
-          const uint64_t al = smem_desc(wl + a_off, kRows * 16, kCoreBytes);
+          for (int kc = 0; kc < nk; ++kc, ++cnt) {
+            const uint32_t st = cnt % kStages;
+            if (!wait_phase(&bar[kQFull + st], (cnt / kStages) & 1, abort_flag, P.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t q0 = sbase + S.q + st * S.q_stage;
+            const uint32_t a_off = (uint32_t)kc * 2 * (kRows * 16);
+            const uint64_t ah = smem_desc(wh + a_off, kRows * 16, kCoreBytes);
+            const uint64_t al = smem_desc(wl + a_off, kRows * 16, kCoreBytes);
+            if constexpr (kBF16) {
 #pragma unroll
-          for (int nh = 0; nh < 2; ++nh) {
-            const uint32_t noff = (uint32_t)nh * nhalf * 16;
-            const uint64_t bh = smem_desc(q0 + noff, (uint32_t)Lp * 16, kCoreBytes);
-            const uint64_t bl = smem_desc(q0 + S.q_part + noff, (uint32_t)Lp * 16, kCoreBytes);
-            const uint32_t d = tmem + (uint32_t)(nh * nhalf);
-            tc_mma(d, ah, bh, idesc, kc > 0 ? 1u : 0u);
-            tc_mma(d, ah, bl, idesc, 1u);
-            tc_mma(d, al, bh, idesc, 1u);
+              for (int nh = 0; nh < 2; ++nh) {
+                const uint32_t noff = (uint32_t)nh * nhalf * 16;
+                const uint64_t bh = smem_desc(q0 + noff, (uint32_t)Lp * 16, kCoreBytes);
+                const uint64_t bl = smem_desc(q0 + S.q_part + noff, (uint32_t)Lp * 16, kCoreBytes);
+                const uint32_t d = tmem + (uint32_t)(nh * nhalf);
+                tc_mma(d, ah, bh, idesc, kc > 0 ? 1u : 0u);
+                tc_mma(d, ah, bl, idesc, 1u);
+                tc_mma(d, al, bh, idesc, 1u);
+              }
+            } else {
+              // this half's columns: hi*hi into acc0, hi*lo + lo*hi into acc1
+              const uint64_t bh = smem_desc(q0, (uint32_t)nhalf * 16, kCoreBytes);
+              const uint64_t bl = smem_desc(q0 + S.q_part, (uint32_t)nhalf * 16, kCoreBytes);
+              tc_mma(tmem, ah, bh, idesc, kc > 0 ? 1u : 0u);
+              tc_mma(tmem + (uint32_t)nhalf, ah, bl, idesc, kc > 0 ? 1u : 0u);
+              tc_mma(tmem + (uint32_t)nhalf, al, bh, idesc, 1u);
+            }
+            tc_commit(&bar[kQEmpty + st]);
           }
-          tc_commit(&bar[kQEmpty + st]);
+          if (!ok) break;
+          tc_commit(&bar[kDFull]);
         }
         if (!ok) break;
-        tc_commit(&bar[kDFull]);
         tc_commit(&bar[kWFree + wb]);
       }
     }
@@ -339,7 +378,7 @@ apply_tc_kernel(const TcApplyParams P) {
     const int cq = (warp - 2) >> 2;            // which quarter of the columns
     const int per = Lp / 4;
     // M = 64: accumulator row r sits in TMEM lane (r/16)*32 + r%16.
-    load_window(smem, S, P, 0, wt, r0, P.c0[0], 0, Lp / 8);
+    load_window<MODE>(smem, S, P, 0, wt, r0, P.c0[0], 0, Lp / 8);
     // Columns [L, Lp) of the second buffer are only ever padding; a window
     // continued from the previous block never writes them, so zero them once
     // (Q's padding rows are zero, but 0 * NaN is not).
@@ -361,10 +400,8 @@ apply_tc_kernel(const TcApplyParams P) {
         // The next window's new columns [kb, L), into the other buffer once
         // the MMAs of block b-1 (its previous user) are done.
         if (b >= 1 && !wait_phase(&bar[kWFree + ib], ((b - 1) >> 1) & 1, abort_flag, P.status)) break;
-        load_window(smem, S, P, ib, wt, r0, P.c0[b + 1], (L - P.nb) / 8, L / 8);
+        load_window<MODE>(smem, S, P, ib, wt, r0, P.c0[b + 1], (L - P.nb) / 8, L / 8);
       }
-      if (!wait_phase(&bar[kDFull], b & 1, abort_flag, P.status)) break;
-      tc_fence_after();
       const int keep = contig ? P.nb : L;      // columns at or past `keep` carry over
       unsigned char* nhi = smem + S.w + (uint32_t)ib * S.w_buf;
       // Lanes 0-15 of the warp hold rows 16sp .. 16sp+15 (M = 64); each
@@ -372,36 +409,57 @@ apply_tc_kernel(const TcApplyParams P) {
       const int half = lane >> 4;
       const int prow = 16 * sp + (lane & 15);
       const bool pvalid = r0 + prow < P.m;
-      for (int j0 = cq * per; j0 < (cq + 1) * per; j0 += 8) {
-        float v[8];
-        __syncwarp();
-        tmem_ld8(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)j0, v);
-        float w[4];
+      bool ok = true;
+      for (int h = 0; h < kPasses; ++h) {
+        const int t = b * kPasses + h;
+        if (!wait_phase(&bar[kDFull], t & 1, abort_flag, P.status)) { ok = false; break; }
+        tc_fence_after();
+        // BF16: this warp's quarter of all Lp columns.  FP16: its share of
+        // the half's nhalf columns, 8 at a time.
+        const int jbeg = kBF16 ? cq * per : h * nhalf + cq * 8;
+        const int jend = kBF16 ? (cq + 1) * per : (h + 1) * nhalf;
+        const int jstep = kBF16 ? 8 : 32;
+        for (int j0 = jbeg; j0 < jend; j0 += jstep) {
+          float v[8];
+          __syncwarp();
+          const uint32_t tl = tmem + ((uint32_t)(32 * sp) << 16);
+          if constexpr (kBF16) {
+            tmem_ld8(tl + (uint32_t)j0, v);
+          } else {
+            float x[8];
+            tmem_ld8(tl + (uint32_t)(j0 - h * nhalf), v);
+            tmem_ld8(tl + (uint32_t)(nhalf + j0 - h * nhalf), x);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) w[u] = __shfl_sync(0xffffffffu, v[4 + u], lane & 15);
-        if (half) {
+            for (int u = 0; u < 8; ++u) v[u] = fmaf(x[u], 1.0f / 2048.0f, v[u]);
+          }
+          float w[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) v[u] = w[u];
-        }
-        if (j0 >= L) continue;                   // padding columns
-        const int jc = j0 + 4 * half;            // this lane's first column
-        if (j0 >= keep) {
-          uint2 h, l;
-          split_pair(v[0], v[1], h.x, l.x);
-          split_pair(v[2], v[3], h.y, l.y);
-          const uint32_t off = (uint32_t)((j0 - P.nb) / 8) * (kRows * 16) + (uint32_t)prow * 16 + 8 * half;
-          *reinterpret_cast<uint2*>(nhi + off) = h;
-          *reinterpret_cast<uint2*>(nhi + S.w_part + off) = l;
-        } else if (pvalid) {
+          for (int u = 0; u < 4; ++u) w[u] = __shfl_sync(0xffffffffu, v[4 + u], lane & 15);
+          if (half) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int gc = c0 + jc + u;
-            if (gc >= 0 && gc < P.n) __stcg(P.A + (int64_t)gc * P.lda + r0 + prow, f32_to_f64(v[u]));
+            for (int u = 0; u < 4; ++u) v[u] = w[u];
+          }
+          if (j0 >= L) continue;                 // padding columns
+          const int jc = j0 + 4 * half;          // this lane's first column
+          if (j0 >= keep) {
+            uint2 hh, ll;
+            split_pair<MODE>(v[0], v[1], hh.x, ll.x);
+            split_pair<MODE>(v[2], v[3], hh.y, ll.y);
+            const uint32_t off = (uint32_t)((j0 - P.nb) / 8) * (kRows * 16) + (uint32_t)prow * 16 + 8 * half;
+            *reinterpret_cast<uint2*>(nhi + off) = hh;
+            *reinterpret_cast<uint2*>(nhi + S.w_part + off) = ll;
+          } else if (pvalid) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int gc = c0 + jc + u;
+              if (gc >= 0 && gc < P.n) __stcg(P.A + (int64_t)gc * P.lda + r0 + prow, f32_to_f64(v[u]));
+            }
           }
         }
+        tc_fence_before();
+        mbar_arrive(&bar[kDEmpty]);
       }
-      tc_fence_before();
-      mbar_arrive(&bar[kDEmpty]);
+      if (!ok) break;
       if (has_next && !contig) {
         // A new p-block: its first window overlaps columns just stored, so
         // every worker's stores come first.
@@ -409,7 +467,7 @@ apply_tc_kernel(const TcApplyParams P) {
         mbar_arrive(&bar[kStored]);
         if (!wait_phase(&bar[kStored], fresh_loads & 1, abort_flag, P.status)) break;
         ++fresh_loads;
-        load_window(smem, S, P, ib, wt, r0, P.c0[b + 1], 0, Lp / 8);
+        load_window<MODE>(smem, S, P, ib, wt, r0, P.c0[b + 1], 0, Lp / 8);
       }
       if (has_next) {
         fence_async_smem();
@@ -439,42 +497,71 @@ bool apply_tc_supported(int L, int Lp, int nb) {
          apply_tc_smem_bytes(Lp) <= 227 * 1024;
 }
 
-cudaError_t launch_apply_tc(const TcApplyParams& P, cudaStream_t s) {
+template <int MODE>
+static cudaError_t launch_mode(const TcApplyParams& P, cudaStream_t s) {
   const size_t smem = apply_tc_smem_bytes(P.Lp);
-  cudaError_t e = cudaFuncSetAttribute(apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(apply_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((P.m + kRows - 1) / kRows);
-  apply_tc_kernel<<<grid, kThreads, smem, s>>>(P);
+  apply_tc_kernel<MODE><<<grid, kThreads, smem, s>>>(P);
   return cudaGetLastError();
 }
 
+cudaError_t launch_apply_tc(const TcApplyParams& P, int mode, cudaStream_t s) {
+  if (mode == ROT_GEMM_SPLIT_BF16) return launch_mode<ROT_GEMM_SPLIT_BF16>(P, s);
+  if (mode == ROT_GEMM_SPLIT_F16) return launch_mode<ROT_GEMM_SPLIT_F16>(P, s);
+  return cudaErrorInvalidValue;
+}
+
 // Q (nblk blocks of Lp x Lp FP64, column n holding k contiguous) split into
-// BF16 hi/lo, written in the order the apply kernel stages it: for block b,
-// chunk kc of 16 k, k-group kg of 8 k, column n, the 8 values k = 16kc+8kg ..
-// +7 form one 16-byte piece at (((b*nk + kc)*2 + kg)*Lp + n)*8.
+// hi/lo, written in the order the apply kernel stages it.
+//   BF16: for block b, chunk kc of 16 k, k-group kg of 8 k and column n, the
+//         8 values k = 16kc+8kg .. +7 form one 16-byte piece at
+//         (((b*nk + kc)*2 + kg)*Lp + n)*8;  x = hi + lo.
+//   FP16: the same per half h of the columns (N = Lp/2 of them): the piece of
+//         column n of the half is at ((((2b + h)*nk + kc)*2 + kg)*N + n)*8;
+//         x = hi + 2^-11 lo.
 __global__ void split_chunked_kernel(const double* __restrict__ Q, uint16_t* __restrict__ hi,
-                                     uint16_t* __restrict__ lo, int Lp, long long total) {
+                                     uint16_t* __restrict__ lo, int Lp, int mode, long long total) {
   const int nk = Lp / kKChunk;
+  const int W = mode == ROT_GEMM_SPLIT_BF16 ? Lp : Lp / 2;     // columns per staged chunk
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int kk = (int)(e & 7);
     const long long r = e >> 3;
-    const int n = (int)(r % Lp);
-    const long long r2 = r / Lp;
+    const int n = (int)(r % W);
+    const long long r2 = r / W;
     const int kg = (int)(r2 & 1);
     const long long r3 = r2 >> 1;
     const int kc = (int)(r3 % nk);
-    const long long b = r3 / nk;
-    const double q = Q[(b * Lp + n) * Lp + kc * kKChunk + kg * 8 + kk];
-    uint16_t h, l;
-    split_f64(q, h, l);
-    hi[e] = h;
-    lo[e] = l;
+    const long long t = r3 / nk;
+    long long b;
+    int col;
+    if (mode == ROT_GEMM_SPLIT_BF16) {
+      b = t;
+      col = n;
+    } else {
+      b = t >> 1;
+      col = (int)(t & 1) * W + n;
+    }
+    const double q = Q[(b * Lp + col) * Lp + kc * kKChunk + kg * 8 + kk];
+    if (mode == ROT_GEMM_SPLIT_BF16) {
+      uint16_t hv, lv;
+      split_f64(q, hv, lv);
+      hi[e] = hv;
+      lo[e] = lv;
+    } else {
+      const __half h = __float2half_rn((float)q);
+      const __half l = __float2half_rn((float)((q - (double)__half2float(h)) * 2048.0));
+      hi[e] = __half_as_ushort(h);
+      lo[e] = __half_as_ushort(l);
+    }
   }
 }
 
-void split_chunked(const double* Q, uint16_t* hi, uint16_t* lo, int Lp, long long nblk, cudaStream_t s) {
-  split_chunked_kernel<<<1024, 256, 0, s>>>(Q, hi, lo, Lp, nblk * Lp * Lp);
+void split_chunked(const double* Q, uint16_t* hi, uint16_t* lo, int Lp, long long nblk, int mode, cudaStream_t s) {
+  split_chunked_kernel<<<1024, 256, 0, s>>>(Q, hi, lo, Lp, mode, nblk * Lp * Lp);
 }
 
 }  // namespace rs

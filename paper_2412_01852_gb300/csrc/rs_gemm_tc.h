@@ -1,5 +1,5 @@
 // rs_gemm_tc.h -- the tcgen05 (TMEM-accumulator) block apply of the
-// accumulated-block variant, split BF16 (rs_gemm_tc.cu).
+// accumulated-block variant, split BF16 and split FP16 (rs_gemm_tc.cu).
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -25,10 +25,11 @@ struct TcApplyParams {
 // Whether the tensor-core apply supports this block shape.
 bool apply_tc_supported(int L, int Lp, int nb);
 size_t apply_tc_smem_bytes(int Lp);
-cudaError_t launch_apply_tc(const TcApplyParams& P, cudaStream_t s);
+// mode: ROT_GEMM_SPLIT_BF16 or ROT_GEMM_SPLIT_F16.
+cudaError_t launch_apply_tc(const TcApplyParams& P, int mode, cudaStream_t s);
 
 // Split Q (nblk blocks of Lp x Lp FP64, column-major) into the BF16 hi/lo
 // operands of launch_apply_tc, in its staging order.
-void split_chunked(const double* Q, uint16_t* hi, uint16_t* lo, int Lp, long long nblk, cudaStream_t s);
+void split_chunked(const double* Q, uint16_t* hi, uint16_t* lo, int Lp, long long nblk, int mode, cudaStream_t s);
 
 }  // namespace rs
