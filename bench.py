@@ -147,6 +147,26 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(base_seed, rank):
+    """Each rank applies its own independent instance (weak scaling, no data exchange)."""
+    return base_seed + rank
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size, steps, units_per_step, seconds):
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return world_size * steps * units_per_step / seconds
+
+
 def cpu_baseline_leg(cfg, seconds):
     """The oracle as it stands (one thread) on row blocks of the same instance."""
     import oracle
@@ -259,7 +279,7 @@ def main():
             dist.barrier()
 
     m, n, k = cfg["m"], cfg["n"], cfg["k"]
-    seed = cfg["seed"] + rank
+    seed = rank_seed(cfg["seed"], rank)
     A, C, S = wl.problem(m, n, k, seed)
     W = wl.rotation_rows(m, n, k)
     Ad = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()
@@ -291,12 +311,8 @@ def main():
     launches = api.launch_count() - l0
     recs = api.trace_stop()
     rs.rot_device_status()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps * W / (ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    value = job_throughput(ws, args.steps, W, ms * 1e-3)
 
     wave = [r for r in recs if r[0] == "wave_f64"]
     kms = sum(r[1] for r in wave) / max(len(wave), 1)
@@ -319,12 +335,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         api.rot_apply_host(A_host, C_host, S_host)
-    el = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([el], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    e2e = {"value": ws * args.e2e_steps * W / el, "unit": UNIT,
+    el = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": job_throughput(ws, args.e2e_steps, W, el), "unit": UNIT,
            "h2d_bytes_per_step": int(A.nbytes + C.nbytes + S.nbytes), "d2h_bytes_per_step": int(A.nbytes),
            "steps": args.e2e_steps}
 

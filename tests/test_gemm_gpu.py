@@ -85,6 +85,21 @@ def test_apply_gemm_within_bound(api, mode, m, n, k, nb, kb):
         assert np.max(np.abs(out - viaq)) <= 16 * (nb + kb) * U64 * np.abs(A).max() * 4
 
 
+@pytest.mark.parametrize("mode", ["f16", "bf16"])
+def test_wide_window_split_modes(api, mode):
+    """Windows wider than the tensor-memory kernel takes (nb + kb = 384) run
+    on the mma.sync kernel; same bound."""
+    m, n, k, nb, kb = 100, 700, 40, 352, 32
+    A, C, S = wl.problem(m, n, k, seed=m + n + k + 1)
+    ref = oracle.rot_sequence(A, C, S)
+    Ad = dev(A)
+    api.rot_apply_gemm(Ad, dev(C), dev(S), nb=nb, kb=kb, mode=mode)
+    torch.cuda.synchronize()
+    api.rot_device_status()
+    rel = row_rel(Ad.cpu().numpy(), ref)
+    assert rel.max() <= bound(mode, k, nb, kb), rel.max()
+
+
 @pytest.mark.parametrize("mode", ["dmma", "f16", "bf16"])
 def test_orthogonality_drift_on_identity(api, mode):
     n, k, nb, kb = 256, 48, 64, 16
