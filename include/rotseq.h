@@ -195,17 +195,33 @@ rot_status rot_form_blocks(int64_t n, int64_t k, const double* C, int64_t ldc, c
  * Algorithm 2's result computed the rs_gemm way: form the blocks
  * (rot_form_blocks, FP64), then update A block by block in the blocks' order,
  * A(:, c0:c0+L) <- A(:, c0:c0+L) * Q_b, with tensor-core matrix products of
- * the given mode (32-row tiles of A, one CTA each, mma.sync).  A stays FP64
- * in memory.  Accuracy against the FP64 result: DMMA within
- * 16*(k+nb+kb)*2^-53 per row; the split modes lose precision in the
- * products (FP16 split: per-row relative error below 8*k*2^-24; BF16 split:
- * about 2^-16 per block product).  Same arguments as rot_apply plus nb, kb
- * (multiples of 16, nb + kb <= 512) and the mode.  Scratch (the blocks and
- * their split copies) comes from the stream-ordered allocator.
+ * the given mode.  The split modes run on tcgen05 (64-row tiles, FP32
+ * accumulators in tensor memory) when nb + kb <= 320, otherwise on mma.sync
+ * (32-row tiles); DMMA runs on mma.sync (m8n8k4 FP64).  A stays FP64 in
+ * memory.  Accuracy against the FP64 result: DMMA within 16*(k+nb+kb)*2^-53
+ * per row; the split modes lose precision in the products (FP16 split:
+ * per-row relative error below 8*k*2^-24; BF16 split: about 2^-16 per block
+ * product).  Same arguments as rot_apply plus nb, kb (multiples of 16,
+ * nb + kb <= 512) and the mode.  Scratch (the blocks and their split copies)
+ * comes from the stream-ordered allocator.
  */
 rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
                           int64_t ldc, const double* S, int64_t lds, int nb, int kb, rot_gemm_mode mode,
                           void* stream);
+
+/* Device bytes rot_apply_gemm_ws needs for these sizes (0 for a quick
+ * return).  Host-only; ROT_EINVAL for the arguments rot_apply_gemm rejects. */
+rot_status rot_apply_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int nb, int kb, rot_gemm_mode mode,
+                                         size_t* bytes);
+
+/* rot_apply_gemm with caller-owned scratch: `workspace` is device memory of
+ * at least rot_apply_gemm_workspace_size() bytes, 256-byte aligned, used by
+ * the queued work until it completes on `stream`.  No allocation; the result
+ * equals rot_apply_gemm's bit for bit.  ROT_EINVAL if the workspace is
+ * missing, too small or misaligned. */
+rot_status rot_apply_gemm_ws(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
+                             int64_t ldc, const double* S, int64_t lds, int nb, int kb, rot_gemm_mode mode,
+                             void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---- batches of independent problems ------------------------------------ */
 
@@ -276,6 +292,19 @@ rot_status rot_apply_tuned(int64_t m, int64_t n, int64_t k, double* A, int64_t l
 
 /* One-shot batch: create a plan, execute it on `stream`, wait, destroy. */
 rot_status rot_apply_batched(int count, const rot_problem* problems, void* stream);
+
+/* Device bytes rot_apply_batched_ws needs for this batch (0 when no problem
+ * has work), with the tiling a plan would pick.  Host-only; ROT_EINVAL for an
+ * invalid problem. */
+rot_status rot_batched_workspace_size(int count, const rot_problem* problems, size_t* bytes);
+
+/* One batch with caller-owned scratch: `workspace` is device memory of at
+ * least rot_batched_workspace_size() bytes, 256-byte aligned.  The launch's
+ * descriptors are copied from host memory before the call returns; the
+ * kernels are queued on `stream` (no allocation, no wait).  The workspace must
+ * stay untouched until they complete.  Same results as rot_apply_batched. */
+rot_status rot_apply_batched_ws(int count, const rot_problem* problems, void* workspace, size_t workspace_bytes,
+                                void* stream);
 
 /*
  * Autotuner: times a small grid of tilings (K in {8,16}, NB in {32,64,128},

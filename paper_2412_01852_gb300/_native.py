@@ -48,6 +48,10 @@ SIGNATURES = {
     "rot_form_blocks_count": (i64, [i64, i64, ci, ci]),
     "rot_form_blocks": (ci, [i64, i64, vp, i64, vp, i64, ci, ci, vp, vp]),
     "rot_apply_gemm": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, ci, ci, ci, vp]),
+    "rot_apply_gemm_workspace_size": (ci, [i64, i64, i64, ci, ci, ci, ctypes.POINTER(sz)]),
+    "rot_apply_gemm_ws": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, ci, ci, ci, vp, sz, vp]),
+    "rot_batched_workspace_size": (ci, [ci, vp, ctypes.POINTER(sz)]),
+    "rot_apply_batched_ws": (ci, [ci, vp, vp, sz, vp]),
     "rot_server_create": (ci, [vp, ctypes.POINTER(vp)]),
     "rot_server_register": (ci, [vp, i64, i64, vp, i64, ctypes.POINTER(ci)]),
     "rot_server_submit": (ci, [vp, ci, i64, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_uint64)]),

@@ -214,6 +214,27 @@ def rot_apply_batched(problems, stream=None):
                                         _stream_handle(stream)), "rot_apply_batched")
 
 
+def batched_workspace_size(problems):
+    """Device bytes rot_apply_batched_ws needs for this list of (A, C, S)."""
+    import ctypes
+    lib = _native.load()
+    arr = _problem_array(problems)
+    n = ctypes.c_size_t(0)
+    _native.check(lib.rot_batched_workspace_size(len(problems), ctypes.cast(arr, ctypes.c_void_p),
+                                                 ctypes.byref(n)), "rot_batched_workspace_size")
+    return n.value
+
+
+def rot_apply_batched_ws(problems, workspace, stream=None):
+    """One launch over the problems with caller-owned scratch (a CUDA uint8 tensor); no wait."""
+    import ctypes
+    lib = _native.load()
+    arr = _problem_array(problems)
+    _native.check(lib.rot_apply_batched_ws(len(problems), ctypes.cast(arr, ctypes.c_void_p),
+                                           workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                           _stream_handle(stream)), "rot_apply_batched_ws")
+
+
 def batch_autotune(problems, stream=None):
     """Time the tiling grid on copies of the batch; returns (tuning dict, ms)."""
     import ctypes
@@ -333,6 +354,28 @@ def rot_apply_gemm(A, C, S, nb=256, kb=64, mode="f16", stream=None):
     m, n, k, pa, lda, pc, ldc, ps, lds = _args(A, C, S, torch.float64)
     _native.check(lib.rot_apply_gemm(m, n, k, pa, lda, pc, ldc, ps, lds, int(nb), int(kb),
                                      _native.GEMM_MODES[mode], _stream_handle(stream)), "rot_apply_gemm")
+    return A
+
+
+def gemm_workspace_size(m, n, k, nb=256, kb=64, mode="f16"):
+    """Device bytes rot_apply_gemm_ws needs (host-only query)."""
+    import ctypes
+    lib = _native.load()
+    out = ctypes.c_size_t(0)
+    _native.check(lib.rot_apply_gemm_workspace_size(int(m), int(n), int(k), int(nb), int(kb),
+                                                    _native.GEMM_MODES[mode], ctypes.byref(out)),
+                  "rot_apply_gemm_workspace_size")
+    return out.value
+
+
+def rot_apply_gemm_ws(A, C, S, workspace, nb=256, kb=64, mode="f16", stream=None):
+    """rot_apply_gemm with caller-owned scratch (a CUDA uint8 tensor of gemm_workspace_size bytes)."""
+    lib = _native.load()
+    m, n, k, pa, lda, pc, ldc, ps, lds = _args(A, C, S, torch.float64)
+    _native.check(lib.rot_apply_gemm_ws(m, n, k, pa, lda, pc, ldc, ps, lds, int(nb), int(kb),
+                                        _native.GEMM_MODES[mode], workspace.data_ptr(),
+                                        workspace.numel() * workspace.element_size(), _stream_handle(stream)),
+                  "rot_apply_gemm_ws")
     return A
 
 

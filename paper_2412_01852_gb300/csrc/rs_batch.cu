@@ -343,6 +343,45 @@ rot_status rot_batch_plan_destroy(rot_batch_plan* plan) {
   return st;
 }
 
+rot_status rot_batched_workspace_size(int count, const rot_problem* problems, size_t* bytes) {
+  if (!bytes || count < 0 || (count > 0 && !problems)) return ROT_EINVAL;
+  *bytes = 0;
+  rot_tuning tu{};
+  rs::tuning_lookup(count, problems, &tu);
+  rs::BatchLayout L;
+  rot_status st = rs::batch_layout(count, problems, tu, &L);
+  if (st != ROT_OK) return st;
+  *bytes = L.idx.empty() ? 0 : L.total;
+  return ROT_OK;
+}
+
+rot_status rot_apply_batched_ws(int count, const rot_problem* problems, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+  if (count < 0 || (count > 0 && !problems)) return ROT_EINVAL;
+  rot_tuning tu{};
+  rs::tuning_lookup(count, problems, &tu);
+  rs::BatchLayout L;
+  rot_status st = rs::batch_layout(count, problems, tu, &L);
+  if (st != ROT_OK) return st;
+  if (L.idx.empty()) return ROT_OK;
+  if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return ROT_EINVAL;
+  unsigned char* base = static_cast<unsigned char*>(workspace);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rs::BatchLaunch B;
+  B.tuning = tu;
+  if (cudaGetDevice(&B.device) != cudaSuccess) return ROT_ECUDA;
+  std::vector<unsigned char> img(L.o_cs);
+  st = rs::batch_image(L, problems, base, img.data(), &B);
+  if (st != ROT_OK) return st;
+  // From pageable memory the copy is staged before the call returns, so the
+  // host image may go out of scope; the kernels that read it follow in order.
+  if (cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return rs::cuda_failed(cudaGetLastError(), "rot_apply_batched_ws: descriptor upload");
+  st = rs::batch_prepare(&B);
+  if (st != ROT_OK) return st;
+  return rs::batch_enqueue(B, s);
+}
+
 rot_status rot_apply_batched(int count, const rot_problem* problems, void* stream) {
   rot_batch_plan* plan = nullptr;
   rot_status st = rot_batch_plan_create(count, problems, nullptr, &plan);

@@ -640,6 +640,90 @@ static rot_status validate_gemm(int64_t m, int64_t n, int64_t k, const void* A, 
 
 }  // namespace rs
 
+namespace rs {
+
+// Workspace of one rs_gemm call: the formation layout, the FP64 blocks, their
+// split copies and a status word, at fixed offsets from a 256-byte aligned base.
+struct GemmLayout {
+  FormLayout F;
+  int L = 0, Lp = 0;
+  int64_t nblk = 0;
+  size_t o_q = 0, o_hi = 0, o_lo = 0, o_status = 0, total = 0;
+};
+
+static void gemm_layout(int64_t n, int64_t k, int nb, int kb, rot_gemm_mode mode, GemmLayout* G) {
+  form_layout(n, k, nb, kb, &G->F);
+  G->L = nb + kb;
+  G->Lp = (int)round_up(G->L, 32);
+  G->nblk = (int64_t)G->F.blocks.size();
+  const size_t q_bytes = (size_t)G->nblk * G->Lp * G->Lp * sizeof(double);
+  const size_t split_bytes = mode == ROT_GEMM_F64_DMMA ? 0 : (size_t)G->nblk * G->Lp * G->Lp * sizeof(uint16_t);
+  G->o_q = round_up((int64_t)G->F.total, 1024);
+  G->o_hi = round_up((int64_t)(G->o_q + q_bytes), 1024);
+  G->o_lo = round_up((int64_t)(G->o_hi + split_bytes), 1024);
+  G->o_status = round_up((int64_t)(G->o_lo + split_bytes), 256);
+  G->total = G->o_status + 256;
+}
+
+// Form the blocks and apply them, all in the workspace at `base`.
+static rot_status gemm_enqueue(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
+                               int64_t ldc, const double* S, int64_t lds, int nb, int kb, rot_gemm_mode mode,
+                               const GemmLayout& G, unsigned char* base, cudaStream_t s) {
+  const FormLayout& F = G.F;
+  const int L = G.L, Lp = G.Lp;
+  const int64_t nblk = G.nblk;
+  const size_t o_hi = G.o_hi, o_lo = G.o_lo, o_status = G.o_status;
+  double* Q = reinterpret_cast<double*>(base + G.o_q);
+  rot_status st = form_blocks_enqueue(n, k, C, ldc, S, lds, nb, kb, F, base, Q, Lp, s);
+  if (st == ROT_OK) {
+    ApplyParams P{};
+    P.A = A; P.lda = lda; P.m = (int)m; P.n = (int)n; P.L = L; P.Lp = Lp; P.nblk = (int)nblk;
+    P.c0 = reinterpret_cast<const int*>(base + F.o_c0);
+    P.Q = Q;
+    P.Qhi = reinterpret_cast<const uint16_t*>(base + o_hi);
+    P.Qlo = reinterpret_cast<const uint16_t*>(base + o_lo);
+    const long long qe = (long long)nblk * Lp * Lp;
+    cudaError_t e = cudaSuccess;
+    const int tr = trace_begin(ROT_KERNEL_GEMM_APPLY, m * (n - 1) * k, s);
+    if (mode != ROT_GEMM_F64_DMMA && apply_tc_supported(L, Lp, nb)) {
+      // tcgen05: 64-row tiles, accumulator in tensor memory.
+      split_chunked(Q, const_cast<uint16_t*>(P.Qhi), const_cast<uint16_t*>(P.Qlo), Lp, nblk, mode, s);
+      TcApplyParams T{};
+      T.A = A; T.lda = lda; T.m = (int)m; T.n = (int)n; T.L = L; T.Lp = Lp; T.nb = nb;
+      T.nblk = (int)nblk;
+      T.c0 = P.c0;
+      T.Qhi = P.Qhi;
+      T.Qlo = P.Qlo;
+      uint32_t cols = 32;
+      while (cols < (uint32_t)Lp) cols <<= 1;
+      T.tmem_cols = cols;
+      T.status = reinterpret_cast<int*>(base + o_status);
+      e = cudaMemsetAsync(T.status, 0, sizeof(int), s);
+      if (e == cudaSuccess) e = launch_apply_tc(T, mode, s);
+      if (e == cudaSuccess) {
+        record_status_async(T.status, s);
+        count_launches(1);
+      }
+    } else if (mode == ROT_GEMM_SPLIT_BF16) {
+      split_kernel<ROT_GEMM_SPLIT_BF16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
+                                                                  const_cast<uint16_t*>(P.Qlo), qe);
+      e = launch_apply<ROT_GEMM_SPLIT_BF16>(P, s);
+    } else if (mode == ROT_GEMM_SPLIT_F16) {
+      split_kernel<ROT_GEMM_SPLIT_F16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
+                                                                 const_cast<uint16_t*>(P.Qlo), qe);
+      e = launch_apply<ROT_GEMM_SPLIT_F16>(P, s);
+    } else {
+      e = launch_apply<ROT_GEMM_F64_DMMA>(P, s);
+    }
+    trace_end(tr, s);
+    count_launches(mode == ROT_GEMM_F64_DMMA ? 1 : 2);
+    if (e != cudaSuccess) st = cuda_failed(e, "rot_apply_gemm: apply kernel");
+  }
+  return st;
+}
+
+}  // namespace rs
+
 extern "C" {
 
 int64_t rot_form_blocks_count(int64_t n, int64_t k, int nb, int kb) {
@@ -665,6 +749,36 @@ rot_status rot_form_blocks(int64_t n, int64_t k, const double* C, int64_t ldc, c
   return st;
 }
 
+rot_status rot_apply_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int nb, int kb, rot_gemm_mode mode,
+                                         size_t* bytes) {
+  if (!bytes) return ROT_EINVAL;
+  *bytes = 0;
+  bool quick;
+  const void* dummy = reinterpret_cast<const void*>(0x100);
+  rot_status v = rs::validate_gemm(m, n, k, dummy, std::max<int64_t>(1, m), dummy, std::max<int64_t>(1, n - 1),
+                                   dummy, std::max<int64_t>(1, n - 1), nb, kb, &quick);
+  if (v != ROT_OK || quick) return v;
+  if (mode != ROT_GEMM_F64_DMMA && mode != ROT_GEMM_SPLIT_BF16 && mode != ROT_GEMM_SPLIT_F16) return ROT_EINVAL;
+  rs::GemmLayout G;
+  rs::gemm_layout(n, k, nb, kb, mode, &G);
+  *bytes = G.total;
+  return ROT_OK;
+}
+
+rot_status rot_apply_gemm_ws(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
+                             int64_t ldc, const double* S, int64_t lds, int nb, int kb, rot_gemm_mode mode,
+                             void* workspace, size_t workspace_bytes, void* stream) {
+  bool quick;
+  rot_status v = rs::validate_gemm(m, n, k, A, lda, C, ldc, S, lds, nb, kb, &quick);
+  if (v != ROT_OK || quick) return v;
+  if (mode != ROT_GEMM_F64_DMMA && mode != ROT_GEMM_SPLIT_BF16 && mode != ROT_GEMM_SPLIT_F16) return ROT_EINVAL;
+  rs::GemmLayout G;
+  rs::gemm_layout(n, k, nb, kb, mode, &G);
+  if (!workspace || workspace_bytes < G.total || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return ROT_EINVAL;
+  return rs::gemm_enqueue(m, n, k, A, lda, C, ldc, S, lds, nb, kb, mode, G, static_cast<unsigned char*>(workspace),
+                          static_cast<cudaStream_t>(stream));
+}
+
 rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
                           int64_t ldc, const double* S, int64_t lds, int nb, int kb, rot_gemm_mode mode,
                           void* stream) {
@@ -673,67 +787,11 @@ rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t ld
   if (v != ROT_OK || quick) return v;
   if (mode != ROT_GEMM_F64_DMMA && mode != ROT_GEMM_SPLIT_BF16 && mode != ROT_GEMM_SPLIT_F16) return ROT_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  rs::FormLayout F;
-  rs::form_layout(n, k, nb, kb, &F);
-  const int L = nb + kb;
-  const int Lp = (int)rs::round_up(L, 32);
-  const int64_t nblk = (int64_t)F.blocks.size();
-  const size_t q_bytes = (size_t)nblk * Lp * Lp * sizeof(double);
-  const size_t split_bytes = mode == ROT_GEMM_F64_DMMA ? 0 : (size_t)nblk * Lp * Lp * sizeof(uint16_t);
-  const size_t o_q = rs::round_up((int64_t)F.total, 1024);
-  const size_t o_hi = rs::round_up((int64_t)(o_q + q_bytes), 1024);
-  const size_t o_lo = rs::round_up((int64_t)(o_hi + split_bytes), 1024);
-  const size_t o_status = rs::round_up((int64_t)(o_lo + split_bytes), 256);
-  const size_t total = o_status + 256;
+  rs::GemmLayout G;
+  rs::gemm_layout(n, k, nb, kb, mode, &G);
   void* ws = nullptr;
-  if (cudaMallocAsync(&ws, total, s) != cudaSuccess) { cudaGetLastError(); return ROT_ENOMEM; }
-  unsigned char* base = static_cast<unsigned char*>(ws);
-  double* Q = reinterpret_cast<double*>(base + o_q);
-  rot_status st = rs::form_blocks_enqueue(n, k, C, ldc, S, lds, nb, kb, F, base, Q, Lp, s);
-  if (st == ROT_OK) {
-    rs::ApplyParams P{};
-    P.A = A; P.lda = lda; P.m = (int)m; P.n = (int)n; P.L = L; P.Lp = Lp; P.nblk = (int)nblk;
-    P.c0 = reinterpret_cast<const int*>(base + F.o_c0);
-    P.Q = Q;
-    P.Qhi = reinterpret_cast<const uint16_t*>(base + o_hi);
-    P.Qlo = reinterpret_cast<const uint16_t*>(base + o_lo);
-    const long long qe = (long long)nblk * Lp * Lp;
-    cudaError_t e = cudaSuccess;
-    const int tr = rs::trace_begin(ROT_KERNEL_GEMM_APPLY, m * (n - 1) * k, s);
-    if (mode != ROT_GEMM_F64_DMMA && rs::apply_tc_supported(L, Lp, nb)) {
-      // tcgen05: 64-row tiles, accumulator in tensor memory.
-      rs::split_chunked(Q, const_cast<uint16_t*>(P.Qhi), const_cast<uint16_t*>(P.Qlo), Lp, nblk, mode, s);
-      rs::TcApplyParams T{};
-      T.A = A; T.lda = lda; T.m = (int)m; T.n = (int)n; T.L = L; T.Lp = Lp; T.nb = nb;
-      T.nblk = (int)nblk;
-      T.c0 = P.c0;
-      T.Qhi = P.Qhi;
-      T.Qlo = P.Qlo;
-      uint32_t cols = 32;
-      while (cols < (uint32_t)Lp) cols <<= 1;
-      T.tmem_cols = cols;
-      T.status = reinterpret_cast<int*>(base + o_status);
-      e = cudaMemsetAsync(T.status, 0, sizeof(int), s);
-      if (e == cudaSuccess) e = rs::launch_apply_tc(T, mode, s);
-      if (e == cudaSuccess) {
-        rs::record_status_async(T.status, s);
-        rs::count_launches(1);
-      }
-    } else if (mode == ROT_GEMM_SPLIT_BF16) {
-      rs::split_kernel<ROT_GEMM_SPLIT_BF16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
-                                                                  const_cast<uint16_t*>(P.Qlo), qe);
-      e = rs::launch_apply<ROT_GEMM_SPLIT_BF16>(P, s);
-    } else if (mode == ROT_GEMM_SPLIT_F16) {
-      rs::split_kernel<ROT_GEMM_SPLIT_F16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
-                                                                 const_cast<uint16_t*>(P.Qlo), qe);
-      e = rs::launch_apply<ROT_GEMM_SPLIT_F16>(P, s);
-    } else {
-      e = rs::launch_apply<ROT_GEMM_F64_DMMA>(P, s);
-    }
-    rs::trace_end(tr, s);
-    rs::count_launches(mode == ROT_GEMM_F64_DMMA ? 1 : 2);
-    if (e != cudaSuccess) st = rs::cuda_failed(e, "rot_apply_gemm: apply kernel");
-  }
+  if (cudaMallocAsync(&ws, G.total, s) != cudaSuccess) { cudaGetLastError(); return ROT_ENOMEM; }
+  rot_status st = rs::gemm_enqueue(m, n, k, A, lda, C, ldc, S, lds, nb, kb, mode, G, static_cast<unsigned char*>(ws), s);
   cudaFreeAsync(ws, s);
   return st;
 }

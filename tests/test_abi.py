@@ -85,3 +85,32 @@ def test_server_argument_checks_without_device(lib):
     assert lib.rot_server_submit(None, 0, 4, None, 1, None, 1, ctypes.byref(t)) == 1
     assert lib.rot_server_wait(None, 1, 0) == 1
     assert lib.rot_server_destroy(None) == 0
+
+
+def test_workspace_size_queries_are_host_only(lib):
+    """Workspace sizes for the caller-owned-scratch entry points need no device."""
+    sz = ctypes.c_size_t(0)
+    assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 64, 16, 1, ctypes.byref(sz)) == 0
+    small = sz.value
+    assert small > 0
+    assert lib.rot_apply_gemm_workspace_size(100, 600, 40, 64, 16, 1, ctypes.byref(sz)) == 0
+    assert sz.value > small                                   # more blocks, more scratch
+    assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 64, 16, 0, ctypes.byref(sz)) == 0
+    assert 0 < sz.value < small                               # DMMA keeps no split copies
+    assert lib.rot_apply_gemm_workspace_size(0, 300, 40, 64, 16, 1, ctypes.byref(sz)) == 0 and sz.value == 0
+    assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 60, 16, 1, ctypes.byref(sz)) == 1   # nb % 16
+    assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 64, 16, 7, ctypes.byref(sz)) == 1   # mode
+    assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 64, 16, 1, None) == 1
+    # a too-small or misaligned caller workspace is refused before any device call
+    assert lib.rot_apply_gemm_ws(100, 300, 40, P, 100, P, 299, P, 299, 64, 16, 1, P, 16, None) == 1
+    assert lib.rot_apply_gemm_ws(100, 300, 40, P, 100, P, 299, P, 299, 64, 16, 1,
+                                 ctypes.c_void_p(0x1008), small, None) == 1
+    arr = (_native.Problem * 2)()
+    for i, (m, n, k) in enumerate([(64, 100, 7), (33, 40, 3)]):
+        arr[i].m, arr[i].n, arr[i].k = m, n, k
+        arr[i].A, arr[i].C, arr[i].S = 0x1000, 0x1000, 0x1000
+        arr[i].lda, arr[i].ldc, arr[i].lds = m, n - 1, n - 1
+    assert lib.rot_batched_workspace_size(2, ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(sz)) == 0
+    assert sz.value > 0
+    assert lib.rot_batched_workspace_size(0, None, ctypes.byref(sz)) == 0 and sz.value == 0
+    assert lib.rot_apply_batched_ws(2, ctypes.cast(arr, ctypes.c_void_p), P, 16, None) == 1

@@ -149,3 +149,21 @@ def test_autotune_leaves_data_alone(rs):
     rs.rot_device_status()
     for (Ad, _, _), (A, C, S) in zip(devs, host):
         assert np.array_equal(bits(Ad.cpu().numpy()), bits(oracle.rot_sequence(A, C, S)))
+
+
+def test_batched_with_caller_workspace(rs):
+    """rot_apply_batched_ws: caller-owned scratch, same bits as the oracle."""
+    from paper_2412_01852_gb300 import api
+    shapes = uneven_shapes(5, 16)
+    host, devs = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A, C, S = wl.problem(m, n, k, seed=3000 + i)
+        host.append((A, C, S))
+        devs.append((dev(A), dev(C), dev(S)))
+    nbytes = api.batched_workspace_size(devs)
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+    api.rot_apply_batched_ws(devs, ws)
+    torch.cuda.synchronize()
+    rs.rot_device_status()
+    for (A, C, S), (Ad, _, _) in zip(host, devs):
+        assert np.array_equal(bits(Ad.cpu().numpy()), bits(oracle.rot_sequence(A, C, S)))

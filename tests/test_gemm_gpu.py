@@ -128,3 +128,19 @@ def test_precision_config_8192_sampled_rows(api, mode):
     api.rot_device_status()
     out = Ad[torch.from_numpy(rows).cuda()].cpu().numpy()
     assert row_rel(out, ref).max() <= bound(mode, k, nb, kb)
+
+
+@pytest.mark.parametrize("mode", ["bf16", "f16", "dmma"])
+def test_caller_workspace_gives_the_same_bits(api, mode):
+    """rot_apply_gemm_ws with caller-owned scratch equals rot_apply_gemm bit for bit."""
+    m, n, k, nb, kb = 100, 300, 40, 64, 16
+    A, C, S = wl.problem(m, n, k, seed=77)
+    Cd, Sd = dev(C), dev(S)
+    a1, a2 = dev(A), dev(A)
+    api.rot_apply_gemm(a1, Cd, Sd, nb=nb, kb=kb, mode=mode)
+    nbytes = api.gemm_workspace_size(m, n, k, nb=nb, kb=kb, mode=mode)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    api.rot_apply_gemm_ws(a2, Cd, Sd, ws, nb=nb, kb=kb, mode=mode)
+    torch.cuda.synchronize()
+    api.rot_device_status()
+    assert torch.equal(a1.view(torch.int64), a2.view(torch.int64))
