@@ -14,6 +14,9 @@ struct WaveOptions {
   int ctas_per_sm = 0;    // resident CTAs per SM (<= occupancy limit)
   int fp64_products = 0;  // 0 default, 1 DMUL, 2 integer pipe
   bool reflectors = false; // the pairs are 2x2 reflectors (tau, nu) instead of (c, s)
+  const int* arrived = nullptr;  // upload progress flags per chunk of arrive_cols columns (FP64 only)
+  int arrive_cols = 0;
+  int* last_done = nullptr;      // per wave-block completion counts of the last p-block
 };
 
 // The FP64 products used when a caller leaves the choice to the library.

@@ -143,51 +143,5 @@ rot_status rot_measure_fp64_peak(double* gflops, double* ms_out) {
   return ROT_OK;
 }
 
-rot_status rot_apply_host(int64_t m, int64_t n, int64_t k, double* A_host, int64_t lda,
-                          const double* C_host, int64_t ldc, const double* S_host, int64_t lds,
-                          void* stream) {
-  if (m < 0 || n < 0 || k < 0 || lda < (m > 1 ? m : 1)) return ROT_EINVAL;
-  const int64_t nm1 = n - 1 > 1 ? n - 1 : 1;
-  if (ldc < nm1 || lds < nm1) return ROT_EINVAL;
-  if (m == 0 || n <= 1 || k == 0) return ROT_OK;
-  if (!A_host || !C_host || !S_host) return ROT_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t a_bytes = (size_t)m * n * sizeof(double);
-  const size_t cs_bytes = (size_t)(n - 1) * k * sizeof(double);
-  double *dA = nullptr, *dC = nullptr, *dS = nullptr;
-  if (cudaMallocAsync((void**)&dA, a_bytes, s) != cudaSuccess ||
-      cudaMallocAsync((void**)&dC, cs_bytes, s) != cudaSuccess ||
-      cudaMallocAsync((void**)&dS, cs_bytes, s) != cudaSuccess) {
-    cudaGetLastError();
-    if (dA) cudaFreeAsync(dA, s);
-    if (dC) cudaFreeAsync(dC, s);
-    cudaStreamSynchronize(s);
-    return ROT_ENOMEM;
-  }
-  rot_status st = ROT_OK;
-  do {
-    if (cudaMemcpy2DAsync(dA, m * sizeof(double), A_host, lda * sizeof(double), m * sizeof(double), n,
-                          cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpy2DAsync(dC, (n - 1) * sizeof(double), C_host, ldc * sizeof(double),
-                          (n - 1) * sizeof(double), k, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpy2DAsync(dS, (n - 1) * sizeof(double), S_host, lds * sizeof(double),
-                          (n - 1) * sizeof(double), k, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-      st = ROT_ECUDA;
-      break;
-    }
-    st = rot_apply(m, n, k, dA, m, dC, n - 1, dS, n - 1, stream);
-    if (st != ROT_OK) break;
-    if (cudaMemcpy2DAsync(A_host, lda * sizeof(double), dA, m * sizeof(double), m * sizeof(double), n,
-                          cudaMemcpyDeviceToHost, s) != cudaSuccess) {
-      st = ROT_ECUDA;
-      break;
-    }
-  } while (0);
-  cudaFreeAsync(dA, s);
-  cudaFreeAsync(dC, s);
-  cudaFreeAsync(dS, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess && st == ROT_OK) st = ROT_ECUDA;
-  return st;
-}
 
 }  // extern "C"

@@ -175,6 +175,10 @@ struct WaveInstance {
   int* done;        // [nchains * G] completed wave-blocks per (chain, p-block)
   const void* tmap; // TMA descriptor of the (c,s) tensor (global memory), batched kernel only
   unsigned long long wait_ns;  // limit of one dependency wait (0: kWaitLimitNs)
+  // Streaming A in and out while the kernel runs (both optional, null = off):
+  const int* arrived;  // arrived[c / arrive_cols] != 0 once columns of that chunk are in A
+  int arrive_cols;
+  int* last_done;      // last_done[b]: chains that finished wave-block b of the last p-block
 };
 
 // The whole problem: every rotation (j, p) with 0 <= j <= n-2, 0 <= p < k.
@@ -306,6 +310,11 @@ __device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap
       if (need > Bp) need = Bp;
       ok = wait_flag_geq(done + g - 1, need, status, lim);
     }
+    // The first p-block reads columns up to w1 + 1 straight from A: when A is
+    // being uploaded while the kernel runs, wait for the chunk holding them
+    // (chunks arrive in column order).
+    if (ok && g == 0 && I.arrived)
+      ok = wait_flag_geq(I.arrived + min(w1 + 1, n - 1) / I.arrive_cols, 1, status, lim);
     if (!ok) set_error(status, kDevTimeoutDependency);
   }
   ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
@@ -407,6 +416,11 @@ __device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap
   if (lane == 0) {
     __threadfence();
     st_release_gpu(done + g, b + 1);
+    if (I.last_done && g == I.G - 1) {
+      // Columns this item finished may now be copied out by another engine.
+      __threadfence_system();
+      atomicAdd(I.last_done + b, 1);
+    }
   }
   return true;
 }

@@ -182,6 +182,9 @@ rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const 
     P.ticket = reinterpret_cast<unsigned long long*>(base + tick_off);
     P.status = reinterpret_cast<int*>(base + tick_off + 64);
     P.total = pl.total;
+    P.arrived = opt.arrived;
+    P.arrive_cols = opt.arrive_cols;
+    P.last_done = opt.last_done;
     const int tr = trace_begin(opt.reflectors ? ROT_KERNEL_REFLECT_F64
                                : sizeof(T) == 8 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32,
                                (long long)m * (n - 1) * k, stream);

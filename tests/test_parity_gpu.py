@@ -226,3 +226,25 @@ def test_left_application_bit_exact(rs, m, n, k, lda):
     after = Abuf.cpu().numpy()
     assert np.array_equal(bits(after[:m]), bits(ref))
     assert np.array_equal(bits(after[m:]), bits(before[m:]))
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("m,n,k", [(100, 77, 21), (257, 530, 40), (33, 9, 5), (64, 1000, 3), (300, 2000, 70)])
+def test_host_buffers_overlapped_copies_bit_exact(rs, m, n, k, pinned):
+    """rot_apply_host: A streamed in by column chunks while the kernel runs and
+    copied back as the last p-block finishes each chunk; same bits as the oracle."""
+    from paper_2412_01852_gb300 import api
+    A, C, S = wl.problem(m, n, k, seed=m + 2 * n + 3 * k)
+    ref = oracle.rot_sequence(A, C, S)
+
+    def host(x):
+        if not pinned:
+            return np.asfortranarray(x.copy())
+        t = torch.empty((x.shape[1], x.shape[0]), dtype=torch.float64, pin_memory=True)
+        h = t.numpy().T
+        h[:] = x
+        return h
+    Ah, Ch, Sh = host(A), host(C), host(S)
+    api.rot_apply_host(Ah, Ch, Sh)
+    rs.rot_device_status()
+    assert np.array_equal(bits(np.ascontiguousarray(Ah)), bits(np.ascontiguousarray(ref)))
