@@ -401,6 +401,15 @@ def _timed_steps(torch, fn, steps, warmup, stream):
     return e0.elapsed_time(e1)
 
 
+def _measured_peaks():
+    """The measured peaks of this machine's GPUs, if present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def run_variant(args):
     import torch
     import paper_2412_01852_gb300 as rs
@@ -476,6 +485,26 @@ def run_variant(args):
                                 "note": "achieved counts the rotations of all blocks on full identity rows "
                                         "(zero waves are skipped, so this overstates executed flops)"}
             line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
+            # The block apply on its own: 2*L^2 flops per row and block per product.
+            akms = kernels.get("gemm_apply", 0.0)
+            L = cfg["nb"] + cfg["kb"]
+            mode = cfg_line["mode"]
+            products = 1 if mode == "dmma" else 3
+            aflops = products * 2.0 * m * L * L * nblk
+            if akms > 0:
+                ap = {"kernel": "block apply (%s)" % ("mma.sync DMMA" if mode == "dmma" else "tcgen05 split " + mode),
+                      "kernel_ms": akms, "achieved": aflops / (akms * 1e-3) / 1e12, "unit": "TFLOP/s"}
+                if mode == "dmma":
+                    ap.update({"bound": "tensor", "peak": None,
+                               "note": "FP64 MMA shares the FP64 pipe; its measured rate is about 1.05 TFLOP/s"})
+                else:
+                    peaks = _measured_peaks()
+                    bf = peaks.get("bf16_tflops")
+                    ap.update({"bound": "tensor", "peak": bf,
+                               "peak_source": "measured bf16 dense burst (FP16 has the same dense rate)"})
+                    if bf:
+                        ap["frac"] = ap["achieved"] / bf
+                line["apply_roofline"] = ap
         print(json.dumps(line), flush=True)
         return
 
