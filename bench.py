@@ -46,11 +46,11 @@ UNIT = "rot-rows/s"
 # summarised in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum),
 # together with a hash of the kernel sources it was taken on.  If the kernel
 # sources change, the number no longer applies and traffic is reported as null.
-# Captured on plain-8192x4096 (0.5123e9 B per launch) and scaled by the
+# Captured on plain-8192x4096 (0.5089e9 B per launch) and scaled by the
 # rotation-rows of plain-8192 (x2.00024): consecutive p-blocks follow each other
 # closely enough that A's columns are still in L2 for the next p-block, so the
 # kernel reads and writes A about once and its traffic grows with n.
-NCU_TRAFFIC = {"bytes": 1.0248e9, "kernel_src_sha": "6e58324d70b724de"}
+NCU_TRAFFIC = {"bytes": 1.0179e9, "kernel_src_sha": "02cf0ba5d1d0949c"}
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -248,6 +248,8 @@ def main():
                     help="plain (default) is the measured line; the others measure the other "
                          "paths of the library on the same GPU")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-fuse-k", type=int, default=192,
+                    help="most sequences fused per matrix per launch in the serving variant (0 = no limit)")
     args = ap.parse_args()
     cfg = dict(wl.WORKLOADS[args.workload])
     cfg["name"] = args.workload
@@ -579,7 +581,8 @@ def run_variant(args):
         sizes = wl.SERVING_SIZES
         per_size = 4
         mats, handles = [], {}
-        srv = api.Server(hbm_budget_bytes=4 << 30, max_inflight=256, streams=8, max_batch=64)
+        srv = api.Server(hbm_budget_bytes=4 << 30, max_inflight=256, streams=8, max_batch=64,
+                         max_fused_k=args.serve_fuse_k)
         for s_i, nsz in enumerate(sizes):
             for j in range(per_size):
                 Ad = _dev_colmajor(torch, wl.matrix(nsz, nsz, seed=7000 + 10 * s_i + j), dev)
@@ -630,7 +633,7 @@ def run_variant(args):
                                             "weights 1/n, k uniform [2,64], seed 5; %d resident matrices"
                                             % len(mats), "requests_per_level": args.serve_requests,
                                 "server": {"hbm_budget_bytes": 4 << 30, "max_inflight": 256, "streams": 8,
-                                           "max_batch": 64}},
+                                           "max_batch": 64, "max_fused_k": args.serve_fuse_k}},
                      "capacity": {"requests_per_s": cap_rps, "p50_ms": st_burst["p50_ms"],
                                   "p99_ms": st_burst["p99_ms"], "mean_batch": st_burst["mean_batch"]},
                      "loads": levels})

@@ -329,6 +329,8 @@ typedef struct {
   int max_inflight;         /* requests admitted and not yet complete */
   int streams;              /* launches that may run at the same time, 1..64 */
   int max_batch;            /* requests per launch */
+  int max_fused_k;          /* most sequences of queued requests on one matrix
+                               fused into one problem; 0 = no limit */
 } rot_server_config;
 
 typedef struct {
@@ -350,8 +352,8 @@ typedef struct {
  * launch of the batched wavefront kernel, and issues it on a free stream;
  * launches on different streams overlap on the device.  A matrix is never in
  * two launches at once, so requests on one matrix apply in submission order;
- * consecutive pending requests on one matrix (up to 64 sequences together)
- * go out as one problem whose sequences are theirs in submission order, which
+ * consecutive pending requests on one matrix (up to cfg->max_fused_k
+ * sequences together, or all of them when it is 0) go out as one problem whose sequences are theirs in submission order, which
  * is the same computation.  A launch's grid is sized to the work items it can
  * run at once, leaving SMs to the launches beside it, and a launch with few
  * items per key uses p-blocks of 8 or 4 sequences.  The paper has no serving

@@ -63,7 +63,7 @@ SIGNATURES = {
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
-                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int)]
+                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_fused_k", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):

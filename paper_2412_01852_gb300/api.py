@@ -261,10 +261,11 @@ class Server:
     done (raises RotError on failure, including a wait that runs out).
     """
 
-    def __init__(self, hbm_budget_bytes=1 << 30, max_inflight=64, streams=4, max_batch=32):
+    def __init__(self, hbm_budget_bytes=1 << 30, max_inflight=64, streams=4, max_batch=32, max_fused_k=192):
         import ctypes
         self._lib = _native.load()
-        cfg = _native.ServerConfig(int(hbm_budget_bytes), int(max_inflight), int(streams), int(max_batch))
+        cfg = _native.ServerConfig(int(hbm_budget_bytes), int(max_inflight), int(streams), int(max_batch),
+                                   int(max_fused_k))
         h = ctypes.c_void_p()
         _native.check(self._lib.rot_server_create(ctypes.cast(ctypes.pointer(cfg), ctypes.c_void_p),
                                                   ctypes.byref(h)), "rot_server_create")

@@ -193,9 +193,6 @@ struct Group {
   std::vector<std::shared_ptr<Request>> reqs;
 };
 
-// Largest number of sequences fused into one problem.
-constexpr int64_t kFuseMaxK = 64;
-
 // Device bytes a launch over these groups needs (layout + compact C/S).
 bool size_launch(Server* S, const std::vector<Group>& gs, BatchLayout* L, std::vector<rot_problem>* probs,
                  size_t* cs_region, size_t* total) {
@@ -246,7 +243,8 @@ void scheduler(Server* S) {
         const int h = r->handle;
         bool can = !blocked[h] && !S->mats[h].busy && S->inflight + nreq < S->cfg.max_inflight &&
                    nreq < S->cfg.max_batch;
-        if (can && gidx[h] >= 0 && groups[gidx[h]].k + r->k > kFuseMaxK) can = false;
+        if (can && gidx[h] >= 0 && S->cfg.max_fused_k > 0 && groups[gidx[h]].k + r->k > S->cfg.max_fused_k)
+          can = false;
         if (!can) {
           blocked[h] = 1;   // later requests on this matrix keep their order
           ++it;
@@ -399,7 +397,7 @@ rot_status rot_server_create(const rot_server_config* cfg, rot_server** out) {
   if (!out || !cfg) return ROT_EINVAL;
   *out = nullptr;
   if (cfg->hbm_budget_bytes < (1u << 20) || cfg->max_inflight < 1 || cfg->streams < 1 || cfg->streams > 64 ||
-      cfg->max_batch < 1)
+      cfg->max_batch < 1 || cfg->max_fused_k < 0)
     return ROT_EINVAL;
   auto* h = new (std::nothrow) rot_server_s;
   if (!h) return ROT_ENOMEM;

@@ -80,6 +80,8 @@ def test_server_argument_checks_without_device(lib):
     assert lib.rot_server_create(ctypes.cast(ctypes.pointer(cfg), ctypes.c_void_p), ctypes.byref(h)) == 1
     cfg = nat.ServerConfig(1 << 30, 4, 65, 4)      # too many streams
     assert lib.rot_server_create(ctypes.cast(ctypes.pointer(cfg), ctypes.c_void_p), ctypes.byref(h)) == 1
+    cfg = nat.ServerConfig(1 << 30, 4, 2, 4, -1)   # negative fusion limit
+    assert lib.rot_server_create(ctypes.cast(ctypes.pointer(cfg), ctypes.c_void_p), ctypes.byref(h)) == 1
     assert lib.rot_server_create(None, ctypes.byref(h)) == 1
     t = ctypes.c_uint64()
     assert lib.rot_server_submit(None, 0, 4, None, 1, None, 1, ctypes.byref(t)) == 1

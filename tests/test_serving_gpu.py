@@ -85,13 +85,16 @@ def test_budget_refusal_and_serialisation(api):
     assert np.array_equal(bits(Ad.cpu().numpy()), bits(exp))
 
 
-def test_fused_requests_on_one_matrix(api):
-    """Requests queued on one matrix go out fused (their sequences concatenated);
-    the result is the same bits as applying them one after another."""
+@pytest.mark.parametrize("max_fused_k", [0, 16])
+def test_fused_requests_on_one_matrix(api, max_fused_k):
+    """Requests queued on one matrix go out fused (their sequences concatenated,
+    up to max_fused_k of them, or all when it is 0); the result is the same
+    bits as applying them one after another."""
     A = wl.matrix(300, 260, seed=9)
     Ad = dev(A)
     exp = A
-    with api.Server(hbm_budget_bytes=256 << 20, max_inflight=64, streams=4, max_batch=64) as srv:
+    with api.Server(hbm_budget_bytes=256 << 20, max_inflight=64, streams=4, max_batch=64,
+                    max_fused_k=max_fused_k) as srv:
         h = srv.register(Ad)
         reqs = [wl.rotations(260, 3 + (q * 7) % 29, seed=90 + q) for q in range(24)]
         ts = [srv.submit(h, C, S) for (C, S) in reqs]     # a burst: later ones queue
@@ -101,7 +104,8 @@ def test_fused_requests_on_one_matrix(api):
         for (C, S) in reqs:
             exp = oracle.rot_sequence(exp, C, S)
         assert st["completed"] == 24
-        assert st["launches"] < 24           # queued requests were fused
+        if max_fused_k == 0:
+            assert st["launches"] < 24       # queued requests were fused
     assert np.array_equal(bits(Ad.cpu().numpy()), bits(exp))
 
 
