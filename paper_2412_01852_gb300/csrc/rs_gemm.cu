@@ -685,7 +685,7 @@ static rot_status gemm_enqueue(int64_t m, int64_t n, int64_t k, double* A, int64
     const long long qe = (long long)nblk * Lp * Lp;
     cudaError_t e = cudaSuccess;
     const int tr = trace_begin(ROT_KERNEL_GEMM_APPLY, m * (n - 1) * k, s);
-    if (mode != ROT_GEMM_F64_DMMA && apply_tc_supported(L, Lp, nb)) {
+    if (mode != ROT_GEMM_F64_DMMA && apply_tc_supported(L, Lp, nb, mode)) {
       // tcgen05: 64-row tiles, accumulator in tensor memory.
       split_chunked(Q, const_cast<uint16_t*>(P.Qhi), const_cast<uint16_t*>(P.Qlo), Lp, nblk, mode, s);
       TcApplyParams T{};

@@ -14,19 +14,22 @@
 // One CTA owns a tile of 64 rows of A (M = 64) and walks the blocks in their
 // order with three roles:
 //   * a TMA producer thread streams Q_b hi/lo (prepared in global memory,
-//     column n holding k contiguous) in chunks of 16 k-rows through three
-//     stages (full/empty mbarriers);
+//     column n holding k contiguous) in chunks of 16 k-rows through four
+//     stages (full/empty mbarriers); the stream is latency-bound, so the
+//     stage count matters (two stages: +25 % time, three: the previous build);
 //   * an MMA thread issues, per chunk, the three products for the two halves
 //     of N (N = Lp/2 each, at most 256) into the TMEM accumulator and commits
 //     each chunk to its stage's empty barrier;
-//   * 16 worker warps keep two window buffers: while block b's products run
-//     they read the nb new columns of block b+1 from A (FP64), split them and
-//     write them into the other buffer; when the accumulator is complete they
-//     read it (tcgen05.ld, each warp its TMEM sub-partition), store block b's
-//     finished columns to A in FP64 and write the kb columns that blocks b
-//     and b+1 share, split again from FP32, as the next window's first
-//     columns.  The first window of a p-block is read whole, after the
-//     previous block's columns are stored.
+//   * 16 worker warps keep the windows: the kb columns a block shares with
+//     the previous one in buffer C, its nb new columns in one of two buffers
+//     N0, N1.  While block b's products run they read the nb new columns of
+//     block b+1 from A (FP64), split them and write them into the other N
+//     buffer; when the accumulator is complete they read it (tcgen05.ld, each
+//     warp its TMEM sub-partition), store block b's finished columns to A in
+//     FP64 and write the kb columns that blocks b and b+1 share, split again
+//     from FP32, into C (block b's products, C's readers, are done by then).
+//     The first window of a p-block is read whole, after the previous
+//     block's columns are stored.
 // The window operands sit in shared memory in the K-major no-swizzle layout
 // of 8-row x 16-byte core matrices.  Every wait is bounded; on a timeout the
 // CTA records an error, every role stops, the producer waits for its copies
@@ -46,7 +49,7 @@ namespace {
 constexpr int kRows = 64;           // rows of A per CTA (the MMA's M)
 constexpr int kWorkers = 16;        // warps that load windows and run the epilogue
 constexpr int kThreads = (2 + kWorkers) * 32;   // + the TMA producer and MMA issuer warps
-constexpr int kStages = 3;          // Q chunks in flight
+constexpr int kStages = 4;          // Q chunks in flight
 constexpr int kKChunk = 16;         // k per MMA instruction (BF16)
 constexpr uint32_t kCoreBytes = 128;  // one core matrix: 8 rows x 16 bytes
 
@@ -172,31 +175,52 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
   }
 }
 
-// Shared-memory plan (byte offsets from the dynamic base, Lp = padded width):
-//   W[2]      two window buffers, each hi then lo, each 64 rows x Lp BF16:
-//             element (m, k) at (k/8)*1024 + m*16 + (k%8)*2
-//   Q[3]      three chunk stages, each hi then lo, each two k-groups of
-//             Lp rows x 16 bytes: element (n, k) at (k/8)*16*Lp + n*16 + (k%8)*2
-//   barriers  q_full[3], q_empty[3], w_ready[2], w_free[2], d_full, d_empty, stored
+// Shared-memory plan (byte offsets from the dynamic base, Lp = padded width,
+// kb = L - nb carried columns, a multiple of 16):
+//   C         window columns [0, kb), hi then lo, 64 rows each
+//   N[2]      window columns [kb, Lp), two buffers, each hi then lo
+//             In each, 8-column group g of the part sits at g*1024, element
+//             (m, k%8) of the group at m*16 + (k%8)*2 (K-major core matrices).
+//   Q[4]      chunk stages, each hi then lo, each two k-groups of Lp rows x
+//             16 bytes: element (n, k) at (k/8)*16*Lp + n*16 + (k%8)*2
+//   barriers  see Bar
 struct Smem {
-  uint32_t w, w_buf, w_part, q, q_stage, q_part, bar, slot, flag, total;
+  uint32_t c, c_part, n, n_buf, n_part, q, q_stage, q_part, bar, slot, flag, total;
 };
-__host__ __device__ inline Smem smem_plan(int Lp) {
+__host__ __device__ inline Smem smem_plan(int Lp, int kb) {
   Smem s{};
-  s.w_part = (uint32_t)kRows * Lp * 2;
-  s.w_buf = 2 * s.w_part;
-  s.w = 0;
+  s.c = 0;
+  s.c_part = (uint32_t)kRows * kb * 2;
+  s.n = 2 * s.c_part;
+  s.n_part = (uint32_t)kRows * (Lp - kb) * 2;
+  s.n_buf = 2 * s.n_part;
   s.q_part = (uint32_t)Lp * kKChunk * 2;
   s.q_stage = 2 * s.q_part;
-  s.q = 2 * s.w_buf;
+  s.q = s.n + 2 * s.n_buf;
   s.bar = s.q + kStages * s.q_stage;
   s.slot = s.bar + 16 * 8;
   s.flag = s.slot + 4;
   s.total = s.flag + 4 + 8;
   return s;
 }
+// Offset of 8-column group g (hi part) of the window in N buffer `buf`
+// (groups below gc = kb/8 are in C), and the distance from hi to lo there.
+__device__ __forceinline__ uint32_t win_group(const Smem& S, int buf, int g, int gc) {
+  return g < gc ? S.c + (uint32_t)g * (kRows * 16) : S.n + (uint32_t)buf * S.n_buf + (uint32_t)(g - gc) * (kRows * 16);
+}
+__device__ __forceinline__ uint32_t win_lo(const Smem& S, int g, int gc) { return g < gc ? S.c_part : S.n_part; }
 
-enum Bar { kQFull = 0, kQEmpty = 3, kWReady = 6, kWFree = 8, kDFull = 10, kDEmpty = 11, kStored = 12 };
+enum Bar {
+  kQFull = 0,
+  kQEmpty = kQFull + kStages,
+  kWReady = kQEmpty + kStages,
+  kWFree = kWReady + 2,
+  kDFull = kWFree + 2,
+  kDEmpty = kDFull + 1,
+  kStored = kDEmpty + 1,
+  kNumBars = kStored + 1
+};
+static_assert(kNumBars <= 16, "barrier area");
 
 // A wait that gives up after the limit or once another role has given up.
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
@@ -208,7 +232,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volat
 }
 
 // Window columns [g_lo*8, g_hi*8) of the block whose window starts at global
-// column c0: FP64 from A, split, into buffer `wbuf`.  Columns outside [0, n),
+// column c0: FP64 from A, split, into C and N buffer `wbuf`.  Columns outside [0, n),
 // at or past L, and rows outside [0, m) are zero.  `wt` is the worker thread;
 // each handles one row and up to kGroupsInFlight 8-column groups at a time,
 // all of whose loads are issued before the first is used.
@@ -220,8 +244,7 @@ __device__ void load_window(unsigned char* smem, const Smem& S, const TcApplyPar
   const int grow = r0 + row;
   const bool rok = grow < P.m;
   const double* arow = P.A + (rok ? grow : 0);
-  unsigned char* hi = smem + S.w + (uint32_t)wbuf * S.w_buf;
-  unsigned char* lo = hi + S.w_part;
+  const int gc = (P.L - P.nb) / 8;
   constexpr int kStep = kWorkers * 32 / kRows;   // threads per row
   for (int g0 = g_lo + wt / kRows; g0 < g_hi; g0 += kGroupsInFlight * kStep) {
     double v[kGroupsInFlight][8];
@@ -244,9 +267,9 @@ __device__ void load_window(unsigned char* smem, const Smem& S, const TcApplyPar
       split_pair<MODE>(f64_to_f32_rz(v[t][2]), f64_to_f32_rz(v[t][3]), h.y, l.y);
       split_pair<MODE>(f64_to_f32_rz(v[t][4]), f64_to_f32_rz(v[t][5]), h.z, l.z);
       split_pair<MODE>(f64_to_f32_rz(v[t][6]), f64_to_f32_rz(v[t][7]), h.w, l.w);
-      const uint32_t off = (uint32_t)g * (kRows * 16) + (uint32_t)row * 16;
-      *reinterpret_cast<uint4*>(hi + off) = h;
-      *reinterpret_cast<uint4*>(lo + off) = l;
+      const uint32_t off = win_group(S, wbuf, g, gc) + (uint32_t)row * 16;
+      *reinterpret_cast<uint4*>(smem + off) = h;
+      *reinterpret_cast<uint4*>(smem + off + win_lo(S, g, gc)) = l;
     }
   }
 }
@@ -261,7 +284,9 @@ apply_tc_kernel(const TcApplyParams P) {
   constexpr int kPasses = kBF16 ? 1 : 2;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int Lp = P.Lp, L = P.L;
-  const Smem S = smem_plan(Lp);
+  const int kb = L - P.nb;                  // carried columns
+  const int gc = kb / 8, kcar = kb / kKChunk;
+  const Smem S = smem_plan(Lp, kb);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S.bar);
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + S.slot);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + S.flag);
@@ -276,7 +301,7 @@ apply_tc_kernel(const TcApplyParams P) {
 
   if (warp == 0) tmem_alloc(slot, ncols);
   if (tid == 32) {
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < kStages; ++i) {
       mbar_init(&bar[kQFull + i], 1);
       mbar_init(&bar[kQEmpty + i], 1);
     }
@@ -295,74 +320,102 @@ apply_tc_kernel(const TcApplyParams P) {
   tc_fence_after();
   const uint32_t tmem = *slot;
 
+  // The producer and MMA threads each issue one long stream of asynchronous
+  // operations from a single thread; that thread's own arithmetic between two
+  // issues does not overlap the tensor pipe, so both loops keep it minimal:
+  // stages and parities advance by counters, copy sources by pointer
+  // increments, and descriptors (whose start address is the low field, in
+  // 16-byte units) by adding offsets to ones built once.
   if (warp == 0) {
-    // ---- producer: Q chunks by TMA, three stages ahead -----------------------------
+    // ---- producer: Q chunks by bulk copy, four stages ahead --------------------------
     if (lane == 0) {
-      uint32_t cnt = 0;
-      for (int t = 0; t < P.nblk * kPasses && !*abort_flag; ++t) {
-        for (int kc = 0; kc < nk; ++kc, ++cnt) {
-          const uint32_t st = cnt % kStages;
-          if (cnt >= (uint32_t)kStages &&
-              !wait_phase(&bar[kQEmpty + st], ((cnt / kStages) - 1) & 1, abort_flag, P.status))
-            break;
-          // The chunk is stored in global memory in exactly its shared-memory
-          // layout: one bulk copy each for hi and lo.
-          mbar_arrive_expect_tx(&bar[kQFull + st], 2 * part_bytes);
-          unsigned char* dst = smem + S.q + st * S.q_stage;
-          const int64_t src = ((int64_t)t * nk + kc) * (part_bytes / 2);
-          bulk_g2s(dst, P.Qhi + src, part_bytes, &bar[kQFull + st]);
-          bulk_g2s(dst + S.q_part, P.Qlo + src, part_bytes, &bar[kQFull + st]);
+      const uint32_t total = (uint32_t)(P.nblk * kPasses * nk);
+      const int64_t step = part_bytes / 2;   // elements of one operand of one chunk
+      const uint16_t* srch = P.Qhi;
+      const uint16_t* srcl = P.Qlo;
+      uint32_t cnt = 0, st = 0, ph = 0;      // ph: parity of the current round over the stages
+      unsigned char* dst = smem + S.q;
+      for (; cnt < total; ++cnt) {
+        if (cnt >= (uint32_t)kStages && !mbar_try_wait(&bar[kQEmpty + st], ph ^ 1) &&
+            !wait_phase(&bar[kQEmpty + st], ph ^ 1, abort_flag, P.status))
+          break;
+        // The chunk is stored in global memory in exactly its shared-memory
+        // layout: one bulk copy each for hi and lo.
+        mbar_arrive_expect_tx(&bar[kQFull + st], 2 * part_bytes);
+        bulk_g2s(dst, srch, part_bytes, &bar[kQFull + st]);
+        bulk_g2s(dst + S.q_part, srcl, part_bytes, &bar[kQFull + st]);
+        srch += step;
+        srcl += step;
+        dst += S.q_stage;
+        if (++st == (uint32_t)kStages) {
+          st = 0;
+          ph ^= 1;
+          dst = smem + S.q;
         }
       }
       // Leave no copy in flight: the last fill of each stage has landed.
-      for (uint32_t st = 0; st < (uint32_t)kStages && st < cnt; ++st) {
-        const uint32_t fills = (cnt - st + kStages - 1) / kStages;   // fills of stage st
-        (void)mbar_wait_bounded(&bar[kQFull + st], (fills - 1) & 1);
+      for (uint32_t s2 = 0; s2 < (uint32_t)kStages && s2 < cnt; ++s2) {
+        const uint32_t fills = (cnt - s2 + kStages - 1) / kStages;   // fills of stage s2
+        (void)mbar_wait_bounded(&bar[kQFull + s2], (fills - 1) & 1);
       }
     }
   } else if (warp == 1) {
     // ---- MMA issuer ------------------------------------------------------------------
     if (lane == 0) {
       const uint32_t idesc = idesc_f32acc(kBF16, kRows, nhalf);
-      uint32_t cnt = 0;
+      // Window operand: C hi and N0 hi, chunk 0; Q operand of stage 0, hi, column 0.
+      const uint64_t dc = smem_desc(sbase + S.c, kRows * 16, kCoreBytes);
+      const uint64_t dn0 = smem_desc(sbase + S.n, kRows * 16, kCoreBytes);
+      const uint64_t dq0 = smem_desc(sbase + S.q, kBF16 ? (uint32_t)Lp * 16 : (uint32_t)nhalf * 16, kCoreBytes);
+      const uint64_t c_part16 = S.c_part >> 4, n_part16 = S.n_part >> 4, n_buf16 = S.n_buf >> 4;
+      const uint64_t q_part16 = S.q_part >> 4, q_stage16 = S.q_stage >> 4;
+      const uint64_t chunk16 = (2 * kRows * 16) >> 4;   // one chunk of the window: two k-groups
+      const uint64_t half16 = (uint64_t)nhalf;          // nhalf columns of 16 bytes
+      uint32_t st = 0, ph = 0;
+      uint64_t dq = dq0;
       bool ok = true;
       for (int b = 0; b < P.nblk && ok; ++b) {
         const int wb = b & 1;
         if (!wait_phase(&bar[kWReady + wb], (b >> 1) & 1, abort_flag, P.status)) break;
-        const uint32_t wh = sbase + S.w + (uint32_t)wb * S.w_buf;
-        const uint32_t wl = wh + S.w_part;
         for (int h = 0; h < kPasses && ok; ++h) {
           const int t = b * kPasses + h;
           if (t >= 1 && !wait_phase(&bar[kDEmpty], (t - 1) & 1, abort_flag, P.status)) { ok = false; break; }
           tc_fence_after();
-          for (int kc = 0; kc < nk; ++kc, ++cnt) {
-            const uint32_t st = cnt % kStages;
-            if (!wait_phase(&bar[kQFull + st], (cnt / kStages) & 1, abort_flag, P.status)) { ok = false; break; }
+          uint64_t ah = dc, al = dc + c_part16;
+          for (int kc = 0; kc < nk; ++kc) {
+            if (kc == kcar) {                  // past the carried columns: the N buffer
+              ah = dn0 + (uint64_t)wb * n_buf16;
+              al = ah + n_part16;
+            }
+            if (!mbar_try_wait(&bar[kQFull + st], ph) && !wait_phase(&bar[kQFull + st], ph, abort_flag, P.status)) {
+              ok = false;
+              break;
+            }
             tc_fence_after();
-            const uint32_t q0 = sbase + S.q + st * S.q_stage;
-            const uint32_t a_off = (uint32_t)kc * 2 * (kRows * 16);
-            const uint64_t ah = smem_desc(wh + a_off, kRows * 16, kCoreBytes);
-            const uint64_t al = smem_desc(wl + a_off, kRows * 16, kCoreBytes);
+            const uint32_t acc = kc > 0 ? 1u : 0u;
             if constexpr (kBF16) {
-#pragma unroll
-              for (int nh = 0; nh < 2; ++nh) {
-                const uint32_t noff = (uint32_t)nh * nhalf * 16;
-                const uint64_t bh = smem_desc(q0 + noff, (uint32_t)Lp * 16, kCoreBytes);
-                const uint64_t bl = smem_desc(q0 + S.q_part + noff, (uint32_t)Lp * 16, kCoreBytes);
-                const uint32_t d = tmem + (uint32_t)(nh * nhalf);
-                tc_mma(d, ah, bh, idesc, kc > 0 ? 1u : 0u);
-                tc_mma(d, ah, bl, idesc, 1u);
-                tc_mma(d, al, bh, idesc, 1u);
-              }
+              // both halves of N: hi*hi + hi*lo + lo*hi into each
+              tc_mma(tmem, ah, dq, idesc, acc);
+              tc_mma(tmem, ah, dq + q_part16, idesc, 1u);
+              tc_mma(tmem, al, dq, idesc, 1u);
+              tc_mma(tmem + (uint32_t)nhalf, ah, dq + half16, idesc, acc);
+              tc_mma(tmem + (uint32_t)nhalf, ah, dq + q_part16 + half16, idesc, 1u);
+              tc_mma(tmem + (uint32_t)nhalf, al, dq + half16, idesc, 1u);
             } else {
               // this half's columns: hi*hi into acc0, hi*lo + lo*hi into acc1
-              const uint64_t bh = smem_desc(q0, (uint32_t)nhalf * 16, kCoreBytes);
-              const uint64_t bl = smem_desc(q0 + S.q_part, (uint32_t)nhalf * 16, kCoreBytes);
-              tc_mma(tmem, ah, bh, idesc, kc > 0 ? 1u : 0u);
-              tc_mma(tmem + (uint32_t)nhalf, ah, bl, idesc, kc > 0 ? 1u : 0u);
-              tc_mma(tmem + (uint32_t)nhalf, al, bh, idesc, 1u);
+              tc_mma(tmem, ah, dq, idesc, acc);
+              tc_mma(tmem + (uint32_t)nhalf, ah, dq + q_part16, idesc, acc);
+              tc_mma(tmem + (uint32_t)nhalf, al, dq, idesc, 1u);
             }
             tc_commit(&bar[kQEmpty + st]);
+            ah += chunk16;
+            al += chunk16;
+            dq += q_stage16;
+            if (++st == (uint32_t)kStages) {
+              st = 0;
+              ph ^= 1;
+              dq = dq0;
+            }
           }
           if (!ok) break;
           tc_commit(&bar[kDFull]);
@@ -383,10 +436,9 @@ apply_tc_kernel(const TcApplyParams P) {
     // continued from the previous block never writes them, so zero them once
     // (Q's padding rows are zero, but 0 * NaN is not).
     for (int e = wt; e < (Lp - L) / 8 * kRows; e += kWorkers * 32) {
-      const uint32_t off = (uint32_t)(L / 8 + e / kRows) * (kRows * 16) + (uint32_t)(e % kRows) * 16;
-      unsigned char* w1 = smem + S.w + S.w_buf;
-      *reinterpret_cast<uint4*>(w1 + off) = make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4*>(w1 + S.w_part + off) = make_uint4(0, 0, 0, 0);
+      const uint32_t off = win_group(S, 1, L / 8 + e / kRows, gc) + (uint32_t)(e % kRows) * 16;
+      *reinterpret_cast<uint4*>(smem + off) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(smem + off + S.n_part) = make_uint4(0, 0, 0, 0);
     }
     fence_async_smem();
     mbar_arrive(&bar[kWReady + 0]);
@@ -403,7 +455,6 @@ apply_tc_kernel(const TcApplyParams P) {
         load_window<MODE>(smem, S, P, ib, wt, r0, P.c0[b + 1], (L - P.nb) / 8, L / 8);
       }
       const int keep = contig ? P.nb : L;      // columns at or past `keep` carry over
-      unsigned char* nhi = smem + S.w + (uint32_t)ib * S.w_buf;
       // Lanes 0-15 of the warp hold rows 16sp .. 16sp+15 (M = 64); each
       // 8-column piece is shared with lanes 16-31, which take its upper half.
       const int half = lane >> 4;
@@ -445,9 +496,10 @@ apply_tc_kernel(const TcApplyParams P) {
             uint2 hh, ll;
             split_pair<MODE>(v[0], v[1], hh.x, ll.x);
             split_pair<MODE>(v[2], v[3], hh.y, ll.y);
-            const uint32_t off = (uint32_t)((j0 - P.nb) / 8) * (kRows * 16) + (uint32_t)prow * 16 + 8 * half;
-            *reinterpret_cast<uint2*>(nhi + off) = hh;
-            *reinterpret_cast<uint2*>(nhi + S.w_part + off) = ll;
+            // into C: this block's products, C's last readers, are complete
+            const uint32_t off = S.c + (uint32_t)((j0 - P.nb) / 8) * (kRows * 16) + (uint32_t)prow * 16 + 8 * half;
+            *reinterpret_cast<uint2*>(smem + off) = hh;
+            *reinterpret_cast<uint2*>(smem + off + S.c_part) = ll;
           } else if (pvalid) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -486,20 +538,23 @@ apply_tc_kernel(const TcApplyParams P) {
 
 }  // namespace
 
-size_t apply_tc_smem_bytes(int Lp) { return smem_plan(Lp).total; }
+size_t apply_tc_smem_bytes(int Lp, int kb) { return smem_plan(Lp, kb).total; }
 
-bool apply_tc_supported(int L, int Lp, int nb) {
+bool apply_tc_supported(int L, int Lp, int nb, int mode) {
   // N = Lp/2 per MMA (a multiple of 16, at most 256; one TMA box of Lp/2 rows);
   // two windows, three chunk stages and the barriers fit in shared memory; nb
   // and L - nb are whole 8-column groups (the carried columns move in 16-byte
   // pieces).
-  return Lp % 32 == 0 && Lp <= 512 && nb % 8 == 0 && L % 8 == 0 && L <= Lp &&
-         apply_tc_smem_bytes(Lp) <= 227 * 1024;
+  // The carried columns are whole chunks of 16 (C is read by whole chunks)
+  // and, in FP16's two passes, all in the second pass (C is rewritten in its
+  // epilogue, after both passes' products).
+  return Lp % 32 == 0 && Lp <= 512 && nb % 8 == 0 && L % 8 == 0 && nb < L && L <= Lp && (L - nb) % 16 == 0 &&
+         (mode == ROT_GEMM_SPLIT_BF16 || nb >= Lp / 2) && apply_tc_smem_bytes(Lp, L - nb) <= 227 * 1024;
 }
 
 template <int MODE>
 static cudaError_t launch_mode(const TcApplyParams& P, cudaStream_t s) {
-  const size_t smem = apply_tc_smem_bytes(P.Lp);
+  const size_t smem = apply_tc_smem_bytes(P.Lp, P.L - P.nb);
   cudaError_t e = cudaFuncSetAttribute(apply_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -23,8 +23,8 @@ struct TcApplyParams {
 };
 
 // Whether the tensor-core apply supports this block shape.
-bool apply_tc_supported(int L, int Lp, int nb);
-size_t apply_tc_smem_bytes(int Lp);
+bool apply_tc_supported(int L, int Lp, int nb, int mode);
+size_t apply_tc_smem_bytes(int Lp, int kb);
 // mode: ROT_GEMM_SPLIT_BF16 or ROT_GEMM_SPLIT_F16.
 cudaError_t launch_apply_tc(const TcApplyParams& P, int mode, cudaStream_t s);
 
