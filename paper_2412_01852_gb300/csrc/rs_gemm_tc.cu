@@ -286,6 +286,12 @@ apply_tc_kernel(const TcApplyParams P) {
   const int Lp = P.Lp, L = P.L;
   const int kb = L - P.nb;                  // carried columns
   const int gc = kb / 8, kcar = kb / kKChunk;
+  // Q_b(k, n) is exactly zero for n < k - kb: each of the block's kb
+  // sequences moves a row's first nonzero at most one column left.  So the
+  // first half of the output columns (n < nhalf) gets nothing from chunks
+  // kc >= kz, whose products are skipped (FP16: those chunks of its first
+  // pass are not even fetched).
+  const int kz = min(Lp / kKChunk, (Lp / 2 + kb + kKChunk - 1) / kKChunk);
   const Smem S = smem_plan(Lp, kb);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S.bar);
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + S.slot);
@@ -329,28 +335,34 @@ apply_tc_kernel(const TcApplyParams P) {
   if (warp == 0) {
     // ---- producer: Q chunks by bulk copy, four stages ahead --------------------------
     if (lane == 0) {
-      const uint32_t total = (uint32_t)(P.nblk * kPasses * nk);
       const int64_t step = part_bytes / 2;   // elements of one operand of one chunk
-      const uint16_t* srch = P.Qhi;
-      const uint16_t* srcl = P.Qlo;
       uint32_t cnt = 0, st = 0, ph = 0;      // ph: parity of the current round over the stages
       unsigned char* dst = smem + S.q;
-      for (; cnt < total; ++cnt) {
-        if (cnt >= (uint32_t)kStages && !mbar_try_wait(&bar[kQEmpty + st], ph ^ 1) &&
-            !wait_phase(&bar[kQEmpty + st], ph ^ 1, abort_flag, P.status))
-          break;
-        // The chunk is stored in global memory in exactly its shared-memory
-        // layout: one bulk copy each for hi and lo.
-        mbar_arrive_expect_tx(&bar[kQFull + st], 2 * part_bytes);
-        bulk_g2s(dst, srch, part_bytes, &bar[kQFull + st]);
-        bulk_g2s(dst + S.q_part, srcl, part_bytes, &bar[kQFull + st]);
-        srch += step;
-        srcl += step;
-        dst += S.q_stage;
-        if (++st == (uint32_t)kStages) {
-          st = 0;
-          ph ^= 1;
-          dst = smem + S.q;
+      bool ok = true;
+      for (int t = 0; t < P.nblk * kPasses && ok; ++t) {
+        // FP16's first pass (t even) stops at chunk kz; everything else runs all nk
+        const int nkt = (!kBF16 && (t & 1) == 0) ? kz : nk;
+        const uint16_t* srch = P.Qhi + (int64_t)t * nk * step;
+        const uint16_t* srcl = P.Qlo + (int64_t)t * nk * step;
+        for (int kc = 0; kc < nkt; ++kc, ++cnt) {
+          if (cnt >= (uint32_t)kStages && !mbar_try_wait(&bar[kQEmpty + st], ph ^ 1) &&
+              !wait_phase(&bar[kQEmpty + st], ph ^ 1, abort_flag, P.status)) {
+            ok = false;
+            break;
+          }
+          // The chunk is stored in global memory in exactly its shared-memory
+          // layout: one bulk copy each for hi and lo.
+          mbar_arrive_expect_tx(&bar[kQFull + st], 2 * part_bytes);
+          bulk_g2s(dst, srch, part_bytes, &bar[kQFull + st]);
+          bulk_g2s(dst + S.q_part, srcl, part_bytes, &bar[kQFull + st]);
+          srch += step;
+          srcl += step;
+          dst += S.q_stage;
+          if (++st == (uint32_t)kStages) {
+            st = 0;
+            ph ^= 1;
+            dst = smem + S.q;
+          }
         }
       }
       // Leave no copy in flight: the last fill of each stage has landed.
@@ -382,7 +394,8 @@ apply_tc_kernel(const TcApplyParams P) {
           if (t >= 1 && !wait_phase(&bar[kDEmpty], (t - 1) & 1, abort_flag, P.status)) { ok = false; break; }
           tc_fence_after();
           uint64_t ah = dc, al = dc + c_part16;
-          for (int kc = 0; kc < nk; ++kc) {
+          const int nkt = (!kBF16 && h == 0) ? kz : nk;
+          for (int kc = 0; kc < nkt; ++kc) {
             if (kc == kcar) {                  // past the carried columns: the N buffer
               ah = dn0 + (uint64_t)wb * n_buf16;
               al = ah + n_part16;
@@ -395,9 +408,11 @@ apply_tc_kernel(const TcApplyParams P) {
             const uint32_t acc = kc > 0 ? 1u : 0u;
             if constexpr (kBF16) {
               // both halves of N: hi*hi + hi*lo + lo*hi into each
-              tc_mma(tmem, ah, dq, idesc, acc);
-              tc_mma(tmem, ah, dq + q_part16, idesc, 1u);
-              tc_mma(tmem, al, dq, idesc, 1u);
+              if (kc < kz) {
+                tc_mma(tmem, ah, dq, idesc, acc);
+                tc_mma(tmem, ah, dq + q_part16, idesc, 1u);
+                tc_mma(tmem, al, dq, idesc, 1u);
+              }
               tc_mma(tmem + (uint32_t)nhalf, ah, dq + half16, idesc, acc);
               tc_mma(tmem + (uint32_t)nhalf, ah, dq + q_part16 + half16, idesc, 1u);
               tc_mma(tmem + (uint32_t)nhalf, al, dq + half16, idesc, 1u);
