@@ -506,6 +506,17 @@ def run_variant(args):
                                "peak_source": "measured bf16 dense burst (FP16 has the same dense rate)"})
                     if bf:
                         ap["frac"] = ap["achieved"] / bf
+                    # The kernel's own ceiling: per 64-row tile and block it
+                    # issues a fixed number of M = 64, N = Lp/2 products over
+                    # two accumulators, whose issue rate is measured here.
+                    Lp = (L + 31) // 32 * 32
+                    nk, kb = Lp // 16, cfg["kb"]
+                    kz = min(nk, -(-(Lp // 2 + kb) // 16))      # chunks with half 0 nonzero
+                    per_block = 6 * nk - 3 * (nk - kz) if mode == "bf16" else 3 * kz + 3 * nk
+                    ns = api.measure_tc_issue(64, Lp // 2, 2, 3000)
+                    floor_ms = nblk * per_block * ns * 1e-6
+                    ap.update({"mma_issue_ns": ns, "mmas_per_tile_block": per_block,
+                               "issue_floor_ms": floor_ms, "frac_of_issue_floor": floor_ms / akms})
                 line["apply_roofline"] = ap
         print(json.dumps(line), flush=True)
         return

@@ -426,6 +426,18 @@ int64_t rot_launch_count(void);
  * time of one probe launch.  Synchronous. */
 rot_status rot_measure_fp64_peak(double* gflops, double* ms);
 
+/* Issue rate of the 5th-generation tensor cores for one product shape
+ * (tcgen05.mma kind::f16, BF16 operands in shared memory, FP32 accumulator in
+ * tensor memory, K = 16): one CTA per SM, one thread issues `mmas` products
+ * from zeroed operands, cycling over `accumulators` independent accumulators
+ * of n columns; *ns_per_mma is the mean time per product from the first issue
+ * to the completion of the last.  m: 64 or 128; n: a multiple of 16 in
+ * [16, 256]; accumulators * n <= 512; mmas in [1, 2^20]; ROT_EINVAL otherwise,
+ * ROT_ETIMEOUT if a completion wait ran out (4 s).  A diagnostic for the block
+ * apply's roofline (rot_apply_gemm issues M = 64, N = Lp/2 products over two
+ * accumulators); synchronous. */
+rot_status rot_measure_tc_issue(int m, int n, int accumulators, int mmas, double* ns_per_mma);
+
 /*
  * Fault-detection self-test (the paper has no counterpart): runs the FP64
  * wavefront kernel on a small scratch problem whose ticket counter starts

@@ -38,6 +38,7 @@ SIGNATURES = {
     "rot_trace_stop": (ci, [vp, ci, ctypes.POINTER(ci)]),
     "rot_launch_count": (ctypes.c_int64, []),
     "rot_measure_fp64_peak": (ci, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "rot_measure_tc_issue": (ci, [ci, ci, ci, ci, ctypes.POINTER(ctypes.c_double)]),
     "rot_batch_plan_create": (ci, [ci, vp, vp, ctypes.POINTER(vp)]),
     "rot_batch_plan_execute": (ci, [vp, vp]),
     "rot_batch_plan_info": (ci, [vp, vp]),

@@ -134,6 +134,16 @@ def measure_fp64_peak():
     return g.value, ms.value
 
 
+def measure_tc_issue(m, n, accumulators, mmas=3000):
+    """Mean ns per tcgen05.mma of shape m x n x 16 (BF16) over `accumulators`
+    independent accumulators, one issuing thread per SM."""
+    import ctypes
+    ns = ctypes.c_double(0)
+    _native.check(_native.load().rot_measure_tc_issue(int(m), int(n), int(accumulators), int(mmas),
+                                                      ctypes.byref(ns)), "rot_measure_tc_issue")
+    return ns.value
+
+
 # ---- batches of independent problems ---------------------------------------------
 
 def _problem_array(problems):

@@ -35,6 +35,7 @@
 // CTA records an error, every role stops, the producer waits for its copies
 // and the tensor memory is freed.
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -551,6 +552,52 @@ apply_tc_kernel(const TcApplyParams P) {
   }
 }
 
+// Issue-rate probe: one thread issues `mmas` products of one shape from zeroed
+// shared-memory operands, cycling over `nacc` independent accumulators, and
+// times first issue to last completion.
+constexpr uint32_t kProbeSmem = 120 * 1024;   // more than half an SM: one CTA per SM
+__global__ void __launch_bounds__(128, 1)
+tc_issue_probe_kernel(int M, int N, int nacc, int mmas, unsigned long long* ns, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 16384);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + 16384 + 8);
+  const int tid = threadIdx.x;
+  // A (M x 16) at 0 and B (N x 16) at 8192, K-major core matrices, all zero.
+  for (int i = tid; i < 16384 / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  if (tid < 32) tmem_alloc(slot, 512);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbarrier_init();
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  if (tid == 0) {
+    const uint32_t sb = smem_u32(smem);
+    const uint64_t a = smem_desc(sb, (uint32_t)M * 16, kCoreBytes);
+    const uint64_t b = smem_desc(sb + 8192, (uint32_t)N * 16, kCoreBytes);
+    const uint32_t idesc = idesc_f32acc(true, M, N);
+    const unsigned long long t0 = globaltimer_ns();
+    int q = 0;
+    for (int i = 0; i < mmas; ++i) {
+      tc_mma(tmem + (uint32_t)(q * N), a, b, idesc, i >= nacc ? 1u : 0u);
+      if (++q == nacc) q = 0;
+    }
+    tc_commit(bar);
+    const bool ok = mbar_wait_bounded(bar, 0);
+    ns[blockIdx.x] = ok ? globaltimer_ns() - t0 : 0ull;
+    if (!ok) set_error(status, kDevTimeoutTma);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid < 32) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
 }  // namespace
 
 size_t apply_tc_smem_bytes(int Lp, int kb) { return smem_plan(Lp, kb).total; }
@@ -635,3 +682,37 @@ void split_chunked(const double* Q, uint16_t* hi, uint16_t* lo, int Lp, long lon
 }
 
 }  // namespace rs
+
+extern "C" rot_status rot_measure_tc_issue(int m, int n, int accumulators, int mmas, double* ns_per_mma) {
+  if (!ns_per_mma || (m != 64 && m != 128) || n < 16 || n > 256 || n % 16 != 0 || accumulators < 1 ||
+      accumulators * n > 512 || mmas < 1 || mmas > (1 << 20))
+    return ROT_EINVAL;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ROT_ECUDA;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  unsigned long long* d_ns = nullptr;
+  if (cudaMalloc(&d_ns, sizeof(unsigned long long) * nsm + sizeof(int)) != cudaSuccess) return ROT_ENOMEM;
+  int* d_status = reinterpret_cast<int*>(d_ns + nsm);
+  rot_status st = ROT_OK;
+  cudaError_t e = cudaFuncSetAttribute(rs::tc_issue_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)rs::kProbeSmem);
+  if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof(int));
+  for (int r = 0; r < 2 && e == cudaSuccess; ++r) {   // the first launch warms up
+    rs::tc_issue_probe_kernel<<<nsm, 128, rs::kProbeSmem>>>(m, n, accumulators, mmas, d_ns, d_status);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  std::vector<unsigned long long> h(nsm);
+  int status = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(h.data(), d_ns, sizeof(unsigned long long) * nsm, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) st = rs::cuda_failed(e, "rot_measure_tc_issue");
+  else if (status != 0) st = ROT_ETIMEOUT;
+  cudaFree(d_ns);
+  rs::count_launches(2);
+  if (st != ROT_OK) return st;
+  double sum = 0;
+  for (int i = 0; i < nsm; ++i) sum += (double)h[i];
+  *ns_per_mma = sum / nsm / mmas;
+  return ROT_OK;
+}

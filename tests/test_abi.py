@@ -89,6 +89,14 @@ def test_server_argument_checks_without_device(lib):
     assert lib.rot_server_destroy(None) == 0
 
 
+def test_tc_issue_probe_argument_checks_without_device(lib):
+    d = ctypes.c_double(0)
+    for args in [(32, 160, 2, 100), (64, 8, 1, 100), (64, 168, 1, 100), (128, 272, 1, 100),
+                 (64, 160, 4, 100), (64, 160, 0, 100), (64, 160, 2, 0), (64, 160, 2, (1 << 20) + 1)]:
+        assert lib.rot_measure_tc_issue(*args, ctypes.byref(d)) == 1, args
+    assert lib.rot_measure_tc_issue(64, 160, 2, 100, None) == 1
+
+
 def test_workspace_size_queries_are_host_only(lib):
     """Workspace sizes for the caller-owned-scratch entry points need no device."""
     sz = ctypes.c_size_t(0)

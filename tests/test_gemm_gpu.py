@@ -144,3 +144,15 @@ def test_caller_workspace_gives_the_same_bits(api, mode):
     torch.cuda.synchronize()
     api.rot_device_status()
     assert torch.equal(a1.view(torch.int64), a2.view(torch.int64))
+
+
+def test_tc_issue_probe(api):
+    """The issue-rate probe runs and is consistent: more independent
+    accumulators never make a product slower, and one product costs between
+    1 ns and 10 us."""
+    one = api.measure_tc_issue(64, 160, 1, 2000)
+    three = api.measure_tc_issue(64, 160, 3, 2000)
+    big = api.measure_tc_issue(128, 256, 2, 2000)
+    for v in (one, three, big):
+        assert 1.0 < v < 10000.0, v
+    assert three <= one * 1.05, (one, three)
