@@ -196,7 +196,8 @@ rot_status rot_form_blocks(int64_t n, int64_t k, const double* C, int64_t ldc, c
  * (rot_form_blocks, FP64), then update A block by block in the blocks' order,
  * A(:, c0:c0+L) <- A(:, c0:c0+L) * Q_b, with tensor-core matrix products of
  * the given mode.  The split modes run on tcgen05 (64-row tiles, FP32
- * accumulators in tensor memory) when nb + kb <= 320, otherwise on mma.sync
+ * accumulators in tensor memory) when nb + kb <= 320 (the FP16 split also
+ * needs nb >= Lp/2, Lp = nb + kb rounded up to 32), otherwise on mma.sync
  * (32-row tiles); DMMA runs on mma.sync (m8n8k4 FP64).  A stays FP64 in
  * memory.  Accuracy against the FP64 result: DMMA within 16*(k+nb+kb)*2^-53
  * per row; the split modes lose precision in the products (FP16 split:
