@@ -69,7 +69,8 @@ def test_form_blocks_match_oracle(api, n, k, nb, kb):
 
 @pytest.mark.parametrize("mode", ["dmma", "f16", "bf16"])
 @pytest.mark.parametrize("m,n,k,nb,kb", [(100, 300, 40, 64, 16), (33, 130, 70, 32, 32),
-                                         (257, 500, 64, 256, 64), (64, 40, 100, 16, 16)])
+                                         (257, 500, 64, 256, 64), (64, 40, 100, 16, 16),
+                                         (90, 200, 50, 16, 48)])
 def test_apply_gemm_within_bound(api, mode, m, n, k, nb, kb):
     A, C, S = wl.problem(m, n, k, seed=m + n + k)
     ref = oracle.rot_sequence(A, C, S)

@@ -249,6 +249,18 @@ def test_form_block_orthogonal_and_structured(n, k, nb, kb, w0, p0):
     assert np.all(jj >= ii - kb)
 
 
+@pytest.mark.parametrize("n,k,nb,kb", [(600, 130, 256, 64), (300, 40, 64, 16), (130, 70, 32, 32),
+                                       (200, 50, 16, 48)])
+def test_every_block_of_a_schedule_has_the_zero_triangle(n, k, nb, kb):
+    """Every block of the apply order, edge blocks and short p-blocks
+    included, is zero at (i, j) for j < i - kb; the tensor-core apply skips
+    the products that only meet these zeros."""
+    C, S = wl.rotations(n, k, seed=41)
+    for w0, p0 in oracle.block_schedule(n, k, nb, kb):
+        ii, jj = np.nonzero(oracle.form_block(C, S, n, w0, nb, p0, kb))
+        assert np.all(jj >= ii - kb), (w0, p0)
+
+
 @pytest.mark.parametrize("m,n,k,nb,kb", [(9, 40, 9, 8, 4), (5, 70, 20, 16, 8), (3, 12, 30, 4, 4),
                                          (16, 300, 64, 64, 16)])
 def test_gemm_regrouping_equals_rotations(m, n, k, nb, kb):
