@@ -2,9 +2,11 @@
 
 The hand-picked shapes of the other parity tests cover the edge cases by
 name; this sweep draws further (m, n, k), leading-dimension slack and block
-sizes from a fixed seed, so each run checks the same 52 cases:
+sizes from a fixed seed, so each run checks the same 68 cases:
   FP64 wavefront        bit-exact vs oracle.rot_sequence
   FP32 wavefront        bit-exact vs oracle.rot_sequence_f32
+  left application      bit-exact vs oracle.rot_sequence_left
+  2x2 reflectors        bit-exact vs oracle.refl_sequence
   block apply           per-row error within each mode's bound
   batch of problems     every problem bit-exact
 """
@@ -78,6 +80,32 @@ def test_random_f32_bit_exact(api, m, n, k, slack):
     ref = oracle.rot_sequence_f32(A32, C32, S32)
     Ad, Abuf = dev(A32, m + slack)
     api.rot_apply_f32(Ad, dev(C32)[0], dev(S32)[0])
+    api.rot_device_status()
+    out = Abuf.cpu().numpy()
+    assert np.array_equal(bits(out[:m, :n]), bits(ref))
+    assert np.all(np.isnan(out[m:, :n]))
+
+
+@pytest.mark.parametrize("m,n,k,slack", draw(505, 8, m_hi=400, n_hi=200))
+def test_random_left_bit_exact(api, m, n, k, slack):
+    A = wl.matrix(m, n, seed=m + 2 * n + k)
+    C, S = wl.rotations(m, k, seed=k + 7)                # rotations mix the m rows
+    ref = oracle.rot_sequence_left(A, C, S)
+    Ad, Abuf = dev(A, m + slack)
+    api.rot_apply_left(Ad, dev(C)[0], dev(S)[0])
+    api.rot_device_status()
+    out = Abuf.cpu().numpy()
+    assert np.array_equal(bits(out[:m, :n]), bits(ref))
+    assert np.all(np.isnan(out[m:, :n]))
+
+
+@pytest.mark.parametrize("m,n,k,slack", draw(606, 8))
+def test_random_reflectors_bit_exact(api, m, n, k, slack):
+    A = wl.matrix(m, n, seed=3 * m + n + k)
+    T, V = wl.reflectors(n, k, seed=m + k)
+    ref = oracle.refl_sequence(A, T, V)
+    Ad, Abuf = dev(A, m + slack)
+    api.rot_apply_reflectors(Ad, dev(T)[0], dev(V)[0])
     api.rot_device_status()
     out = Abuf.cpu().numpy()
     assert np.array_equal(bits(out[:m, :n]), bits(ref))
