@@ -196,6 +196,53 @@ def test_f64_paper_shaped_8192_sampled_rows(rs):
     assert float(((n1 - n0).abs() / n0).max()) <= 8 * k * 2.0 ** -53 * 4
 
 
+def _sample_rows(m, seed):
+    r = np.random.default_rng(seed)
+    return np.unique(np.concatenate([[0, 31, 32, 63, 64, m - 1], r.choice(m, 26, replace=False)]))
+
+
+def test_f32_precision_8192_sampled_rows(rs):
+    """The FP32 workload the bench times (A 8192 x 8192, k = 192, C/S rounded
+    to FP32), in its launch configuration: sampled rows bit-exact against the
+    FP32 oracle (rows are independent), and every row within 8*k*2^-24 of
+    the FP64 oracle's row on the sample."""
+    cfg = wl.WORKLOADS["precision-8192"]
+    m, n, k = cfg["m"], cfg["n"], cfg["k"]
+    A, C, S = wl.problem(m, n, k, seed=cfg["seed"])
+    A32, C32, S32 = A.astype(np.float32), C.astype(np.float32), S.astype(np.float32)
+    rows = _sample_rows(m, 78)
+    ref32 = oracle.rot_sequence_f32(A32[rows], C32, S32)
+    ref64 = oracle.rot_sequence(A[rows], C, S)
+    Ad = torch.from_numpy(np.ascontiguousarray(A32.T)).cuda().t()
+    Cd = torch.from_numpy(np.ascontiguousarray(C32.T)).cuda().t()
+    Sd = torch.from_numpy(np.ascontiguousarray(S32.T)).cuda().t()
+    rs.rot_apply_f32(Ad, Cd, Sd)
+    rs.rot_device_status()
+    out = Ad[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert np.array_equal(bits(out), bits(ref32))
+    rel = np.linalg.norm(out.astype(np.float64) - ref64, axis=1) / np.linalg.norm(ref64, axis=1)
+    assert rel.max() <= 8 * k * U32
+
+
+def test_reflectors_8192_sampled_rows(rs):
+    """The reflector workload the bench times (A 8192 x 8192, k = 192):
+    sampled rows bit-exact against the reflector oracle."""
+    from paper_2412_01852_gb300 import api
+    cfg = wl.WORKLOADS["plain-8192"]
+    m, n, k = cfg["m"], cfg["n"], cfg["k"]
+    A = wl.matrix(m, n, cfg["seed"])
+    T, V = wl.reflectors(n, k, cfg["seed"])
+    rows = _sample_rows(m, 79)
+    ref = oracle.refl_sequence(A[rows], T, V)
+    Ad = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+    Td = torch.from_numpy(np.ascontiguousarray(T.T)).cuda().t()
+    Vd = torch.from_numpy(np.ascontiguousarray(V.T)).cuda().t()
+    api.rot_apply_reflectors(Ad, Td, Vd)
+    rs.rot_device_status()
+    out = Ad[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert np.array_equal(bits(out), bits(ref))
+
+
 @pytest.mark.parametrize("m,n,k", SHAPES)
 def test_reflectors_bit_exact(rs, m, n, k):
     from paper_2412_01852_gb300 import api
