@@ -54,6 +54,16 @@ __device__ __forceinline__ void set_error(int* status, int code) {
 // ---- L2-coherent data movement (A is shared between SMs through L2) ---------
 template <typename T> __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
 template <typename T> __device__ __forceinline__ void st_cg(T* p, T v) { __stcg(p, v); }
+// An L2 policy that keeps lines resident ahead of others (evict_last), and an
+// FP32 store under it.
+__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void st_l2_keep(float* p, float v, unsigned long long policy) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(policy) : "memory");
+}
 
 // ---- mbarrier ---------------------------------------------------------------
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {

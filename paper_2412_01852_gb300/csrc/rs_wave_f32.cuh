@@ -54,6 +54,11 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
   if (!ok) return false;
 
   const int64_t lda = I.lda;
+  // Retired columns are read again by the next p-block about two items
+  // later; storing them as evict_last keeps more of them in L2 (measured:
+  // 2.5 % less time at 8192 x 8192, k = 192; the p-blocks in flight span
+  // more columns than L2 holds).
+  const unsigned long long keep = l2_evict_last_policy();
   T* arow[R];
   bool rowok[R];
 #pragma unroll
@@ -149,7 +154,7 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
         // column w + 1 - KMAX (>= own_lo and >= 0 in an interior tile) retires
 #pragma unroll
         for (int r = 0; r < R; ++r)
-          if (rowok[r]) st_cg(ps + r * 32, win[r][u % U]);
+          if (rowok[r]) st_l2_keep(ps + r * 32, win[r][u % U], keep);
         ps += lda;
       }
     } else {
