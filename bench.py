@@ -248,6 +248,8 @@ def main():
                     help="plain (default) is the measured line; the others measure the other "
                          "paths of the library on the same GPU")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-batch", type=int, default=64, help="requests per launch in the serving variant")
+    ap.add_argument("--serve-streams", type=int, default=8, help="server streams in the serving variant")
     ap.add_argument("--serve-fuse-k", type=int, default=192,
                     help="most sequences fused per matrix per launch in the serving variant (0 = no limit)")
     args = ap.parse_args()
@@ -592,8 +594,8 @@ def run_variant(args):
         sizes = wl.SERVING_SIZES
         per_size = 4
         mats, handles = [], {}
-        srv = api.Server(hbm_budget_bytes=4 << 30, max_inflight=256, streams=8, max_batch=64,
-                         max_fused_k=args.serve_fuse_k)
+        srv = api.Server(hbm_budget_bytes=4 << 30, max_inflight=256, streams=args.serve_streams,
+                         max_batch=args.serve_batch, max_fused_k=args.serve_fuse_k)
         for s_i, nsz in enumerate(sizes):
             for j in range(per_size):
                 Ad = _dev_colmajor(torch, wl.matrix(nsz, nsz, seed=7000 + 10 * s_i + j), dev)
@@ -643,8 +645,9 @@ def run_variant(args):
                      "config": {"workload": "serving: Poisson arrivals, square A with n in {128..4096} "
                                             "weights 1/n, k uniform [2,64], seed 5; %d resident matrices"
                                             % len(mats), "requests_per_level": args.serve_requests,
-                                "server": {"hbm_budget_bytes": 4 << 30, "max_inflight": 256, "streams": 8,
-                                           "max_batch": 64, "max_fused_k": args.serve_fuse_k}},
+                                "server": {"hbm_budget_bytes": 4 << 30, "max_inflight": 256,
+                                           "streams": args.serve_streams, "max_batch": args.serve_batch,
+                                           "max_fused_k": args.serve_fuse_k}},
                      "capacity": {"requests_per_s": cap_rps, "p50_ms": st_burst["p50_ms"],
                                   "p99_ms": st_burst["p99_ms"], "mean_batch": st_burst["mean_batch"]},
                      "loads": levels})
