@@ -47,6 +47,11 @@ bool encode_tile_map_2d(CUtensorMap* map, const void* base, bool is_double, uint
 bool encode_tile_map_2d_b16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
                             uint64_t row_pitch_bytes, uint32_t box_inner, uint32_t box_outer);
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per (kernel, device): function attributes belong to a
+// device's context.
+cudaError_t smem_opt_in(const void* kernel, int bytes);
+
 // Record a failed CUDA call for rot_last_error(); returns ROT_ECUDA.
 rot_status cuda_failed(cudaError_t e, const char* where);
 void note_error(const char* what);

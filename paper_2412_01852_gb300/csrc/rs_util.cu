@@ -21,6 +21,20 @@ rot_status cuda_failed(cudaError_t e, const char* where) {
 }
 
 void note_error(const char* what) { snprintf(g_last_error, sizeof g_last_error, "%s", what); }
+
+cudaError_t smem_opt_in(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void*, int>, int>> done;   // (kernel, device) -> bytes
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  for (const auto& d : done)
+    if (d.first.first == kernel && d.first.second == dev && d.second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.push_back({{kernel, dev}, bytes});
+  return e;
+}
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 struct TraceEntry {

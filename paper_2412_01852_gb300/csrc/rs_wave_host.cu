@@ -111,11 +111,7 @@ static cudaError_t launch_wave(const WaveProblem& P, const CUtensorMap& map, cud
   using SM = WaveSmem<T, KMAX, NBT>;
   auto kfn = wave_kernel<T, KMAX, NBT, WARPS, OP>;
   const int smem = WARPS * SM::kWarpBytes;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  });
+  const cudaError_t attr_err = smem_opt_in(reinterpret_cast<const void*>(kfn), smem);
   if (attr_err != cudaSuccess) return attr_err;
   int dev = 0, nsm = 0, occ = 0;
   cudaGetDevice(&dev);
@@ -224,11 +220,7 @@ static cudaError_t launch_wave_f32(const WaveProblem& P, const CUtensorMap& map,
   using SM = WaveSmem<float, kF32Kmax, kF32NBT>;
   auto kfn = wave_f32_kernel<kF32Kmax, kF32R, kWarps, kF32MinBlocks>;
   const int smem = kWarps * SM::kWarpBytes;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  });
+  const cudaError_t attr_err = smem_opt_in(reinterpret_cast<const void*>(kfn), smem);
   if (attr_err != cudaSuccess) return attr_err;
   int dev = 0, nsm = 0, occ = 0;
   cudaGetDevice(&dev);
