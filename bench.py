@@ -46,11 +46,11 @@ UNIT = "rot-rows/s"
 # summarised in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum),
 # together with a hash of the kernel sources it was taken on.  If the kernel
 # sources change, the number no longer applies and traffic is reported as null.
-# Captured on plain-8192x4096 (0.5089e9 B per launch) and scaled by the
+# Captured on plain-8192x4096 (0.5103e9 B per launch) and scaled by the
 # rotation-rows of plain-8192 (x2.00024): consecutive p-blocks follow each other
 # closely enough that A's columns are still in L2 for the next p-block, so the
 # kernel reads and writes A about once and its traffic grows with n.
-NCU_TRAFFIC = {"bytes": 1.0179e9, "kernel_src_sha": "02cf0ba5d1d0949c"}
+NCU_TRAFFIC = {"bytes": 1.0207e9, "kernel_src_sha": "89379a2d22527eb6"}
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
