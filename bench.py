@@ -244,7 +244,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=512)
     ap.add_argument("--variant", default="plain",
                     choices=["plain", "f32", "gemm-f16", "gemm-bf16", "gemm-dmma", "batched", "serving",
-                             "reflectors"],
+                             "reflectors", "left"],
                     help="plain (default) is the measured line; the others measure the other "
                          "paths of the library on the same GPU")
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -543,6 +543,33 @@ def run_variant(args):
                      "roofline": {"bound": "alu", "kernel": "wave_kernel<double, reflect>", "kernel_ms": kms,
                                   "achieved": 6.0 * W / (kms * 1e-3) / 1e12, "peak": fp64_peak,
                                   "unit": "TFLOP/s"}})
+        line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
+        print(json.dumps(line), flush=True)
+        return
+
+    if args.variant == "left":
+        # Rotations mixing the rows of A (C, S are (m-1) x k): A is transposed in
+        # 32x32 shared-memory tiles, the column kernel runs, and it is
+        # transposed back.  The step time includes both transposes.
+        cfg = wl.WORKLOADS["plain-8192"]
+        m, n, k = cfg["m"], cfg["n"], cfg["k"]
+        A = wl.matrix(m, n, cfg["seed"])
+        C, S = wl.rotations(m, k, cfg["seed"])
+        W = wl.rotation_rows(n, m, k)                   # n columns, each rotated through m rows
+        Ad, Cd, Sd = (_dev_colmajor(torch, X, dev) for X in (A, C, S))
+        api.trace_start()
+        ms = _timed_steps(torch, lambda: api.rot_apply_left(Ad, Cd, Sd), args.steps, args.warmup, stream)
+        recs = api.trace_stop()
+        rs.rot_device_status()
+        kms = [r[1] for r in recs if r[0] == "wave_f64"]
+        kms = sum(kms) / len(kms)
+        line.update({"value": args.steps * W / (ms * 1e-3), "ms_per_step": ms / args.steps, "dtype": "f64",
+                     "config": {"workload": "left application: A 8192x8192 N(0,1), C/S 8191x192 from uniform "
+                                            "angles acting on rows, seed 2", "m": m, "n": n, "k": k},
+                     "kernel_ms_per_step": {"wave_f64": kms, "transposes": ms / args.steps - kms},
+                     "roofline": {"bound": "alu", "kernel": "wave_kernel<double> (on the transpose)",
+                                  "kernel_ms": kms, "achieved": 6.0 * W / (kms * 1e-3) / 1e12,
+                                  "peak": fp64_peak, "unit": "TFLOP/s"}})
         line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
         print(json.dumps(line), flush=True)
         return
