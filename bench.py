@@ -386,6 +386,21 @@ def _dev_colmajor(torch, a, dev, dtype=None):
     return t if dtype is None else t.to(dtype)
 
 
+def _orth_drift(torch, apply_fn, n, dtype, dev):
+    """max |Q^T Q - I| for Q = the variant applied to the n x n identity (the
+    precision workload's orthogonality check), Q^T Q formed in FP64."""
+    Q = torch.eye(n, dtype=dtype, device=dev).t().contiguous().t()
+    apply_fn(Q)
+    torch.cuda.synchronize()
+    Qd = Q.double()
+    M = Qd.t() @ Qd
+    M.diagonal().sub_(1.0)
+    drift = float(M.abs().max())
+    del Q, Qd, M
+    torch.cuda.empty_cache()
+    return drift
+
+
 def _row_rel(torch, out, ref):
     d = torch.linalg.norm((out.double() - ref), dim=1)
     return float((d / torch.linalg.norm(ref, dim=1)).max())
@@ -445,6 +460,8 @@ def run_variant(args):
             rs.rot_apply_f32(once, C32, S32)
             err = _row_rel(torch, once, ref)
             fn = lambda: rs.rot_apply_f32(A32, C32, S32)
+            drift = _orth_drift(torch, lambda Q: rs.rot_apply_f32(Q, C32, S32), n, torch.float32, dev)
+            drift_bound = 8 * k * 2.0 ** -24
             kind, peak, dtype = "wave_f32", fp32_peak, "f32"
             cfg_line = {"workload": "precision-8192 FP32: A 8192x8192, C/S 8191x192 rounded to FP32", "m": m,
                         "n": n, "k": k}
@@ -456,6 +473,10 @@ def run_variant(args):
             err = _row_rel(torch, once, ref)
             work = rs.colmajor(A64)
             fn = lambda: api.rot_apply_gemm(work, C64, S64, nb=nb, kb=kb, mode=mode)
+            drift = _orth_drift(torch, lambda Q: api.rot_apply_gemm(Q, C64, S64, nb=nb, kb=kb, mode=mode), n,
+                                torch.float64, dev)
+            drift_bound = {"dmma": 10 * n * 2.0 ** -53, "f16": 8 * k * 2.0 ** -24,
+                           "bf16": 8 * -(-k // kb) * 2.0 ** -16}[mode]
             kind, peak, dtype = "form_blocks", fp64_peak, {"f16": "f16x2", "bf16": "bf16x2", "dmma": "f64"}[mode]
             cfg_line = {"workload": "precision-8192 accumulated blocks: A 8192x8192, k=192, nb=%d, kb=%d, %s"
                                     % (nb, kb, mode), "m": m, "n": n, "k": k, "nb": nb, "kb": kb, "mode": mode}
@@ -472,7 +493,10 @@ def run_variant(args):
         steps_traced = max(len(v) for v in by.values())
         per_step = {kname: sum(v) / steps_traced for kname, v in by.items()}
         line.update({"value": args.steps * W / (ms * 1e-3), "ms_per_step": ms / args.steps, "dtype": dtype,
-                     "config": cfg_line, "max_row_rel_err_vs_fp64_path": err, "kernel_ms_per_step": per_step})
+                     "config": cfg_line, "max_row_rel_err_vs_fp64_path": err,
+                     "orthogonality_identity": {"max_abs_QtQ_minus_I": drift, "bound": drift_bound,
+                                                "input": "I_%d" % n},
+                     "kernel_ms_per_step": per_step})
         if args.variant == "f32":
             kms = kernels["wave_f32"]
             line["roofline"] = {"bound": "alu", "achieved": 6.0 * W / (kms * 1e-3) / 1e12, "peak": peak,
