@@ -244,7 +244,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=512)
     ap.add_argument("--variant", default="plain",
                     choices=["plain", "f32", "gemm-f16", "gemm-bf16", "gemm-dmma", "batched", "serving",
-                             "reflectors", "left"],
+                             "reflectors", "left", "small-k"],
                     help="plain (default) is the measured line; the others measure the other "
                          "paths of the library on the same GPU")
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -568,6 +568,70 @@ def run_variant(args):
                                   "achieved": 6.0 * W / (kms * 1e-3) / 1e12, "peak": fp64_peak,
                                   "unit": "TFLOP/s"}})
         line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
+        print(json.dumps(line), flush=True)
+        return
+
+    if args.variant == "small-k":
+        # Few sequences: one HBM pass over A carries little arithmetic, so FP32
+        # is bound by HBM; FP64 (0.375 flop/B at k = 1 against a machine balance
+        # near 0.19) stays bound by the FP64 pipe.  L2 is flushed (a 256 MiB
+        # write) before every timed run, which is timed alone.
+        cfg = wl.WORKLOADS["plain-8192"]
+        m, n = cfg["m"], cfg["n"]
+        A = wl.matrix(m, n, cfg["seed"])
+        flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+        peaks = _measured_peaks()
+        hbm = peaks.get("hbm_gbs")
+
+        def timed_alone(fn, reps):
+            for _ in range(3):
+                fn()
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return float(np.median(ts))
+
+        rows = []
+        A32 = _dev_colmajor(torch, A.astype(np.float32), dev)
+        A64 = _dev_colmajor(torch, A, dev)
+        for prec, kk in (("f32", 1), ("f32", 2), ("f32", 4), ("f32", 8), ("f64", 1)):
+            C, S = wl.rotations(n, kk, cfg["seed"])
+            if prec == "f32":
+                Cd, Sd = (_dev_colmajor(torch, X.astype(np.float32), dev) for X in (C, S))
+                fn = lambda: rs.rot_apply_f32(A32, Cd, Sd)
+                esz, fpeak = 4, fp32_peak
+            else:
+                Cd, Sd = (_dev_colmajor(torch, X, dev) for X in (C, S))
+                fn = lambda: rs.rot_apply(A64, Cd, Sd)
+                esz, fpeak = 8, fp64_peak
+            ms = timed_alone(fn, max(args.steps, 10))
+            Wk = wl.rotation_rows(m, n, kk)
+            nbytes = 2 * m * n * esz + 2 * (n - 1) * kk * esz      # A read and written once, C and S read
+            row = {"precision": prec, "k": kk, "ms": ms, "rot_rows_per_s": Wk / (ms * 1e-3),
+                   "tflops": 6.0 * Wk / (ms * 1e-3) / 1e12, "frac_of_nominal_flops": 6.0 * Wk / (ms * 1e-3) / 1e12 / fpeak,
+                   "hbm_gbs": nbytes / (ms * 1e-3) / 1e9, "bytes": nbytes}
+            if hbm:
+                row["frac_of_measured_hbm"] = row["hbm_gbs"] / hbm
+            rows.append(row)
+        rs.rot_device_status()
+        first = rows[0]
+        line.update({"value": first["rot_rows_per_s"], "ms_per_step": first["ms"], "dtype": "f32",
+                     "config": {"workload": "small k: A 8192x8192 N(0,1) (FP32 and FP64), C/S 8191xk from uniform "
+                                            "angles, k in {1,2,4,8} (FP32) and 1 (FP64), seed 2",
+                                "m": m, "n": n, "l2": "flushed before every timed run (256 MiB write)"},
+                     "per_k": rows,
+                     "roofline": {"bound": "hbm", "kernel": "wave_f32_kernel at k = 1",
+                                  "achieved": first["hbm_gbs"], "peak": hbm, "unit": "GB/s",
+                                  "frac": first.get("frac_of_measured_hbm"),
+                                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)",
+                                  "algorithmic_bytes": first["bytes"]}})
         print(json.dumps(line), flush=True)
         return
 

@@ -40,6 +40,14 @@ template <typename T>
 rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
                       const T* S, int64_t lds, cudaStream_t stream, const WaveOptions& opt);
 
+// The single-p-block column stream (rs_stream.cu) for k <= 8: whether it
+// takes this problem, and the call.
+template <typename T>
+bool stream_fits(int64_t m, int64_t n, int64_t k, const T* A, int64_t lda);
+template <typename T>
+rot_status stream_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
+                        const T* S, int64_t lds, cudaStream_t stream);
+
 bool encode_tile_map_2d(CUtensorMap* map, const void* base, bool is_double, uint64_t inner,
                         uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
                         uint32_t box_outer);

@@ -1,0 +1,88 @@
+// rs_stream.cu -- host side of the single-p-block column stream
+// (rs_stream.cuh): rot_apply and rot_apply_f32 take it for k <= 8.
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rs_internal.h"
+#include "rs_stream.cuh"
+
+namespace rs {
+namespace {
+
+inline int64_t round_up256(int64_t x) { return (x + 255) / 256 * 256; }
+
+template <typename T, int KR>
+rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc, const T* S,
+                         int64_t lds, cudaStream_t s) {
+  using SS = StreamShape<T, KR>;
+  constexpr bool kF64 = sizeof(T) == 8;
+  const int64_t W2 = 2 * SS::KP;                   // elements per (c,s) row
+  const int64_t cs_rows = n + k;                   // row j + p <= n + k - 3, plus the TMA's reach
+  const int64_t cs_bytes = cs_rows * W2 * (int64_t)sizeof(T);
+  const int64_t st_off = round_up256(cs_bytes);
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, (size_t)(st_off + 256), s) != cudaSuccess) {
+    cudaGetLastError();
+    return ROT_ENOMEM;
+  }
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  T* cs = reinterpret_cast<T*>(base);
+  int* status = reinterpret_cast<int*>(base + st_off);
+  rot_status st = ROT_OK;
+  do {
+    cudaError_t e = cudaMemsetAsync(base, 0, (size_t)(st_off + sizeof(int)), s);
+    if (e != cudaSuccess) { st = cuda_failed(e, "stream: memset"); break; }
+    dim3 rb(32, 8);
+    dim3 rg((unsigned)((n - 1 + 31) / 32), (unsigned)((k + 7) / 8));
+    repack_cs_kernel<T><<<rg, rb, 0, s>>>(C, ldc, S, lds, (int)n, (int)k, cs, W2, 0);
+    CUtensorMap amap, csmap;
+    if (!encode_tile_map_2d(&amap, A, kF64, (uint64_t)m, (uint64_t)n, (uint64_t)lda * sizeof(T), 32, SS::CB) ||
+        !encode_tile_map_2d(&csmap, cs, kF64, (uint64_t)W2, (uint64_t)cs_rows, (uint64_t)W2 * sizeof(T),
+                            (uint32_t)W2, SS::CB)) {
+      note_error("stream: cuTensorMapEncodeTiled failed");
+      st = ROT_ECUDA;
+      break;
+    }
+    auto kfn = stream_kernel<T, KR>;
+    e = smem_opt_in(reinterpret_cast<const void*>(kfn), SS::kSmem);
+    if (e != cudaSuccess) { st = cuda_failed(e, "stream: shared-memory opt-in"); break; }
+    const int tr = trace_begin(kF64 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32, m * (n - 1) * k, s);
+    kfn<<<(unsigned)((m + 31) / 32), 32, SS::kSmem, s>>>(amap, csmap, A, lda, (int)m, (int)n, (int)k, status);
+    trace_end(tr, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { st = cuda_failed(e, "stream: kernel launch"); break; }
+    record_status_async(status, s);
+    count_launches(3);
+  } while (0);
+  cudaFreeAsync(scratch, s);
+  return st;
+}
+
+}  // namespace
+
+template <typename T>
+bool stream_fits(int64_t m, int64_t n, int64_t k, const T* A, int64_t lda) {
+  // One p-block of at most 8 sequences; TMA needs a 16-byte aligned base and
+  // column pitch, and the boxes (32 rows, up to 27 columns) inside the matrix.
+  return k >= 1 && k <= 8 && m >= 32 && n >= 32 && (reinterpret_cast<uintptr_t>(A) % 16) == 0 &&
+         ((uint64_t)lda * sizeof(T)) % 16 == 0;
+}
+
+template <typename T>
+rot_status stream_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc, const T* S,
+                        int64_t lds, cudaStream_t s) {
+  if (k == 1) return stream_launch<T, 1>(m, n, k, A, lda, C, ldc, S, lds, s);
+  if (k == 2) return stream_launch<T, 2>(m, n, k, A, lda, C, ldc, S, lds, s);
+  if (k <= 4) return stream_launch<T, 4>(m, n, k, A, lda, C, ldc, S, lds, s);
+  return stream_launch<T, 8>(m, n, k, A, lda, C, ldc, S, lds, s);
+}
+
+template bool stream_fits<double>(int64_t, int64_t, int64_t, const double*, int64_t);
+template bool stream_fits<float>(int64_t, int64_t, int64_t, const float*, int64_t);
+template rot_status stream_apply<double>(int64_t, int64_t, int64_t, double*, int64_t, const double*, int64_t,
+                                         const double*, int64_t, cudaStream_t);
+template rot_status stream_apply<float>(int64_t, int64_t, int64_t, float*, int64_t, const float*, int64_t,
+                                        const float*, int64_t, cudaStream_t);
+
+}  // namespace rs

@@ -1,0 +1,129 @@
+// rs_stream.cuh -- the wavefront of a single p-block (k <= 8 sequences) as a
+// column stream.
+//
+// With one p-block there is no dependency between row strips, and the only
+// parallelism Algorithm 2 leaves is across rows (each row's rotations form
+// one sequential chain, Section 1).  At small k a wave carries little
+// arithmetic, so the kernel's time is the latency of bringing each column in.
+// Each warp owns 32 rows (one per lane) and streams all columns through a
+// ring of S stages in shared memory; each stage is filled by two TMA copies:
+// CB columns of its 32 rows, and the (c,s) pairs of the CB waves that take
+// those columns in.  S*CB columns are in flight per warp, enough to hide the
+// memory latency behind the rotations.
+//
+// Column q lives in window slot q % U (U = KR + 1).  Wave w (from -1, when
+// column 0 enters, on) takes in column w + 1 and applies rotations
+// l = 0..k-1 to columns (j, j+1), j = w - l, in increasing l, where
+// 0 <= j <= n-2 (Algorithm 3's order, the same operations per element as
+// Algorithm 2); column w + 1 - KR is then final and is stored.  Tiles hold a
+// multiple of U columns, so every slot index is a compile-time constant.
+#pragma once
+#include "rs_wave.cuh"
+
+namespace rs {
+
+template <typename T, int KR>
+struct StreamShape {
+  static constexpr int U = KR + 1;                      // window slots
+  static constexpr int CB = U * ((20 + U - 1) / U);     // columns per tile, a multiple of U
+  static constexpr int S = 8;                           // tiles in flight
+  // (c,s) rows are padded to 16 bytes (a TMA box's inner extent).
+  static constexpr int KP = (int)(2 * KR * sizeof(T)) >= 16 ? KR : (int)(16 / (2 * sizeof(T)));
+  static constexpr int kABytes = 32 * CB * (int)sizeof(T);
+  static constexpr int kCsBytes = CB * 2 * KP * (int)sizeof(T);
+  static constexpr int kAStage = (kABytes + 127) / 128 * 128;    // TMA destinations 128-byte aligned
+  static constexpr int kCsStage = (kCsBytes + 127) / 128 * 128;
+  static constexpr int kStage = kAStage + kCsStage;
+  static constexpr int kSmem = S * kStage + S * 8;
+};
+
+// One tile: CB waves.  FULL: every rotation of every wave exists (k == KR and
+// the tile lies inside the triangle-free part), so no predicates.
+template <typename T, int KR, bool FULL>
+__device__ __forceinline__ void stream_tile(T (&win)[KR + 1], const T* at, const typename Pair<T>::type* cs,
+                                            int w0, int k, int n, bool rowok, T* arow, int64_t lda, int lane) {
+  using SS = StreamShape<T, KR>;
+  using V2 = typename Pair<T>::type;
+  constexpr int U = SS::U, CB = SS::CB, KP = SS::KP;
+#pragma unroll
+  for (int i = 0; i < CB; ++i) {
+    const int w = w0 + i;
+    win[i % U] = at[i * 32 + lane];              // column w + 1
+#pragma unroll
+    for (int l = 0; l < KR; ++l) {
+      const int j = w - l;
+      if (FULL || (l < k && j >= 0 && j <= n - 2)) {   // the same in every lane
+        const V2 p = cs[i * KP + l];
+        rotate(win[((i - 1 - l) % U + U) % U], win[((i - l) % U + U) % U], p.x, p.y);
+      }
+    }
+    const int q = w + 1 - KR;                    // final: its last rotation was at wave q + k - 1
+    if (rowok && (FULL || (q >= 0 && q <= n - 1))) st_cg(arow + (int64_t)q * lda, win[(i + 1) % U]);
+  }
+}
+
+template <typename T, int KR>
+__global__ void __launch_bounds__(32)
+stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap csmap, T* A,
+              int64_t lda, int m, int n, int k, int* status) {
+  using SS = StreamShape<T, KR>;
+  using V2 = typename Pair<T>::type;
+  constexpr int U = SS::U, CB = SS::CB, S = SS::S;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * SS::kStage);
+  const int lane = threadIdx.x;
+  const int c = blockIdx.x;                     // 32-row strip
+  const int row = c * 32 + lane;
+  const bool rowok = row < m;
+  T* const arow = A + (rowok ? row : 0);
+  // Waves -1 .. n-2+KR: after the last one, column n-1 has been stored.
+  const int ntiles = (n + KR + CB - 1) / CB;
+  if (lane == 0) {
+    prefetch_tmap(&amap);
+    prefetch_tmap(&csmap);
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+    fence_mbarrier_init();
+  }
+  __syncwarp();
+  // Tile t: columns [t*CB, (t+1)*CB) of the strip, and the (c,s) rows of
+  // waves t*CB - 1 .. t*CB + CB - 2 (row -1 reads as zeros).
+  auto issue = [&](int t) {
+    const int s = t % S;
+    unsigned char* st = smem + s * SS::kStage;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar[s], SS::kABytes + SS::kCsBytes);
+    tma_load_2d(st, &amap, &bar[s], c * 32, t * CB);
+    tma_load_2d(st + SS::kAStage, &csmap, &bar[s], 0, t * CB - 1);
+  };
+  if (lane == 0)
+    for (int t = 0; t < S && t < ntiles; ++t) issue(t);
+
+  T win[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) win[u] = T(0);
+  int t = 0;
+  for (; t < ntiles; ++t) {
+    const int s = t % S;
+    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)(t / S) & 1u);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) set_error(status, kDevTimeoutTma);
+      break;
+    }
+    const T* at = reinterpret_cast<const T*>(smem + s * SS::kStage);             // [column i][lane]
+    const V2* cs = reinterpret_cast<const V2*>(smem + s * SS::kStage + SS::kAStage);  // [wave i][pair l]
+    const int w0 = t * CB - 1;
+    // Interior: every wave's rotations j = w-l, l < KR, lie in [0, n-2].
+    if (k == KR && w0 - (KR - 1) >= 0 && w0 + CB - 1 <= n - 2)
+      stream_tile<T, KR, true>(win, at, cs, w0, k, n, rowok, arow, lda, lane);
+    else
+      stream_tile<T, KR, false>(win, at, cs, w0, k, n, rowok, arow, lda, lane);
+    __syncwarp();                                // every lane has read the stage
+    if (lane == 0 && t + S < ntiles) issue(t + S);
+  }
+  // On a timeout, let the copies still in flight land before leaving.
+  if (t < ntiles && lane == 0) {
+    for (int r = t + 1; r < ntiles && r < t + S; ++r) (void)mbar_wait_bounded(&bar[r % S], (uint32_t)(r / S) & 1u);
+  }
+}
+
+}  // namespace rs
