@@ -12,10 +12,16 @@ namespace {
 
 inline int64_t round_up256(int64_t x) { return (x + 255) / 256 * 256; }
 
+// Rows per lane.  One (more warps: with a few warps per SM, each warp's issue
+// rate bounds the stream).
+template <typename T, int KR>
+constexpr int stream_rows() { return 1; }
+
 template <typename T, int KR>
 rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc, const T* S,
                          int64_t lds, cudaStream_t s) {
-  using SS = StreamShape<T, KR>;
+  constexpr int R = stream_rows<T, KR>();
+  using SS = StreamShape<T, KR, R>;
   constexpr bool kF64 = sizeof(T) == 8;
   const int64_t W2 = 2 * SS::KP;                   // elements per (c,s) row
   const int64_t cs_rows = n + k;                   // row j + p <= n + k - 3, plus the TMA's reach
@@ -31,24 +37,26 @@ rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, con
   int* status = reinterpret_cast<int*>(base + st_off);
   rot_status st = ROT_OK;
   do {
-    cudaError_t e = cudaMemsetAsync(base, 0, (size_t)(st_off + sizeof(int)), s);
+    // Pairs the repack does not write are only read by rotations that do not exist.
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e != cudaSuccess) { st = cuda_failed(e, "stream: memset"); break; }
     dim3 rb(32, 8);
     dim3 rg((unsigned)((n - 1 + 31) / 32), (unsigned)((k + 7) / 8));
     repack_cs_kernel<T><<<rg, rb, 0, s>>>(C, ldc, S, lds, (int)n, (int)k, cs, W2, 0);
     CUtensorMap amap, csmap;
-    if (!encode_tile_map_2d(&amap, A, kF64, (uint64_t)m, (uint64_t)n, (uint64_t)lda * sizeof(T), 32, SS::CB) ||
+    if (!encode_tile_map_2d(&amap, A, kF64, (uint64_t)m, (uint64_t)n, (uint64_t)lda * sizeof(T), 32 * R, SS::CB) ||
         !encode_tile_map_2d(&csmap, cs, kF64, (uint64_t)W2, (uint64_t)cs_rows, (uint64_t)W2 * sizeof(T),
                             (uint32_t)W2, SS::CB)) {
       note_error("stream: cuTensorMapEncodeTiled failed");
       st = ROT_ECUDA;
       break;
     }
-    auto kfn = stream_kernel<T, KR>;
+    auto kfn = stream_kernel<T, KR, R>;
     e = smem_opt_in(reinterpret_cast<const void*>(kfn), SS::kSmem);
     if (e != cudaSuccess) { st = cuda_failed(e, "stream: shared-memory opt-in"); break; }
     const int tr = trace_begin(kF64 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32, m * (n - 1) * k, s);
-    kfn<<<(unsigned)((m + 31) / 32), 32, SS::kSmem, s>>>(amap, csmap, A, lda, (int)m, (int)n, (int)k, status);
+    kfn<<<(unsigned)((m + 32 * R - 1) / (32 * R)), 32, SS::kSmem, s>>>(amap, csmap, A, lda, (int)m, (int)n, (int)k,
+                                                                       status);
     trace_end(tr, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) { st = cuda_failed(e, "stream: kernel launch"); break; }
@@ -64,8 +72,9 @@ rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, con
 template <typename T>
 bool stream_fits(int64_t m, int64_t n, int64_t k, const T* A, int64_t lda) {
   // One p-block of at most 8 sequences; TMA needs a 16-byte aligned base and
-  // column pitch, and the boxes (32 rows, up to 27 columns) inside the matrix.
-  return k >= 1 && k <= 8 && m >= 32 && n >= 32 && (reinterpret_cast<uintptr_t>(A) % 16) == 0 &&
+  // column pitch, and the boxes (up to 64 rows, up to 63 columns) inside the
+  // matrix.
+  return k >= 1 && k <= 8 && m >= 64 && n >= 64 && (reinterpret_cast<uintptr_t>(A) % 16) == 0 &&
          ((uint64_t)lda * sizeof(T)) % 16 == 0;
 }
 

@@ -5,11 +5,13 @@
 // parallelism Algorithm 2 leaves is across rows (each row's rotations form
 // one sequential chain, Section 1).  At small k a wave carries little
 // arithmetic, so the kernel's time is the latency of bringing each column in.
-// Each warp owns 32 rows (one per lane) and streams all columns through a
+// Each warp owns 32R rows (R per lane) and streams all columns through a
 // ring of S stages in shared memory; each stage is filled by two TMA copies:
-// CB columns of its 32 rows, and the (c,s) pairs of the CB waves that take
-// those columns in.  S*CB columns are in flight per warp, enough to hide the
-// memory latency behind the rotations.
+// CB columns of its rows, and the (c,s) pairs of the CB waves that take those
+// columns in.  S*CB columns are in flight per warp, enough to hide the memory
+// latency behind the rotations.  With one warp per SMSP or fewer, a wave's
+// dependent FP chain is what a warp waits on; R = 2 gives it two independent
+// chains per wave (and one (c,s) load and store address for two rows).
 //
 // Column q lives in window slot q % U (U = KR + 1).  Wave w (from -1, when
 // column 0 enters, on) takes in column w + 1 and applies rotations
@@ -22,14 +24,19 @@
 
 namespace rs {
 
-template <typename T, int KR>
+template <typename T, int KR, int R>
 struct StreamShape {
   static constexpr int U = KR + 1;                      // window slots
-  static constexpr int CB = U * ((20 + U - 1) / U);     // columns per tile, a multiple of U
+  // Columns per tile, a multiple of U.  A tile costs about 0.2 us on top of
+  // its waves (barrier, copies), so FP32 with small windows takes long tiles;
+  // a window of 8 keeps the unrolled tile within the instruction cache, and
+  // FP64 keeps its ring small enough for two CTAs per SM.
+  static constexpr int kTarget = (sizeof(T) == 4 && KR <= 4) ? 60 : 20;
+  static constexpr int CB = U * ((kTarget + U - 1) / U);
   static constexpr int S = 8;                           // tiles in flight
   // (c,s) rows are padded to 16 bytes (a TMA box's inner extent).
   static constexpr int KP = (int)(2 * KR * sizeof(T)) >= 16 ? KR : (int)(16 / (2 * sizeof(T)));
-  static constexpr int kABytes = 32 * CB * (int)sizeof(T);
+  static constexpr int kABytes = 32 * R * CB * (int)sizeof(T);
   static constexpr int kCsBytes = CB * 2 * KP * (int)sizeof(T);
   static constexpr int kAStage = (kABytes + 127) / 128 * 128;    // TMA destinations 128-byte aligned
   static constexpr int kCsStage = (kCsBytes + 127) / 128 * 128;
@@ -39,43 +46,55 @@ struct StreamShape {
 
 // One tile: CB waves.  FULL: every rotation of every wave exists (k == KR and
 // the tile lies inside the triangle-free part), so no predicates.
-template <typename T, int KR, bool FULL>
-__device__ __forceinline__ void stream_tile(T (&win)[KR + 1], const T* at, const typename Pair<T>::type* cs,
-                                            int w0, int k, int n, bool rowok, T* arow, int64_t lda, int lane) {
-  using SS = StreamShape<T, KR>;
+template <typename T, int KR, int R, bool FULL>
+__device__ __forceinline__ void stream_tile(T (&win)[R][KR + 1], const T* at, const typename Pair<T>::type* cs,
+                                            int w0, int k, int n, const bool (&rowok)[R], T* arow, int64_t lda,
+                                            int lane) {
+  using SS = StreamShape<T, KR, R>;
   using V2 = typename Pair<T>::type;
   constexpr int U = SS::U, CB = SS::CB, KP = SS::KP;
+  // Stores of the interior go through a pointer advanced one column per wave.
+  T* ps = arow + (int64_t)(w0 + 1 - KR) * lda;
 #pragma unroll
   for (int i = 0; i < CB; ++i) {
     const int w = w0 + i;
-    win[i % U] = at[i * 32 + lane];              // column w + 1
+#pragma unroll
+    for (int r = 0; r < R; ++r) win[r][i % U] = at[(i * R + r) * 32 + lane];   // column w + 1
 #pragma unroll
     for (int l = 0; l < KR; ++l) {
       const int j = w - l;
       if (FULL || (l < k && j >= 0 && j <= n - 2)) {   // the same in every lane
         const V2 p = cs[i * KP + l];
-        rotate(win[((i - 1 - l) % U + U) % U], win[((i - l) % U + U) % U], p.x, p.y);
+#pragma unroll
+        for (int r = 0; r < R; ++r) rotate(win[r][((i - 1 - l) % U + U) % U], win[r][((i - l) % U + U) % U], p.x, p.y);
       }
     }
     const int q = w + 1 - KR;                    // final: its last rotation was at wave q + k - 1
-    if (rowok && (FULL || (q >= 0 && q <= n - 1))) st_cg(arow + (int64_t)q * lda, win[(i + 1) % U]);
+    if (FULL || (q >= 0 && q <= n - 1)) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (rowok[r]) st_cg(ps + 32 * r, win[r][(i + 1) % U]);
+    }
+    ps += lda;
   }
 }
 
-template <typename T, int KR>
+template <typename T, int KR, int R>
 __global__ void __launch_bounds__(32)
 stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap csmap, T* A,
               int64_t lda, int m, int n, int k, int* status) {
-  using SS = StreamShape<T, KR>;
+  using SS = StreamShape<T, KR, R>;
   using V2 = typename Pair<T>::type;
   constexpr int U = SS::U, CB = SS::CB, S = SS::S;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * SS::kStage);
   const int lane = threadIdx.x;
-  const int c = blockIdx.x;                     // 32-row strip
-  const int row = c * 32 + lane;
-  const bool rowok = row < m;
-  T* const arow = A + (rowok ? row : 0);
+  const int c = blockIdx.x;                     // strip of 32R rows
+  bool rowok[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) rowok[r] = c * 32 * R + r * 32 + lane < m;
+  // Row of slot r: arow + 32r (only dereferenced where rowok[r]).
+  T* const arow = A + (int64_t)c * 32 * R + lane;
   // Waves -1 .. n-2+KR: after the last one, column n-1 has been stored.
   const int ntiles = (n + KR + CB - 1) / CB;
   if (lane == 0) {
@@ -92,15 +111,17 @@ stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
     unsigned char* st = smem + s * SS::kStage;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&bar[s], SS::kABytes + SS::kCsBytes);
-    tma_load_2d(st, &amap, &bar[s], c * 32, t * CB);
+    tma_load_2d(st, &amap, &bar[s], c * 32 * R, t * CB);
     tma_load_2d(st + SS::kAStage, &csmap, &bar[s], 0, t * CB - 1);
   };
   if (lane == 0)
     for (int t = 0; t < S && t < ntiles; ++t) issue(t);
 
-  T win[U];
+  T win[R][U];
 #pragma unroll
-  for (int u = 0; u < U; ++u) win[u] = T(0);
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int u = 0; u < U; ++u) win[r][u] = T(0);
   int t = 0;
   for (; t < ntiles; ++t) {
     const int s = t % S;
@@ -109,14 +130,14 @@ stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
       if (lane == 0) set_error(status, kDevTimeoutTma);
       break;
     }
-    const T* at = reinterpret_cast<const T*>(smem + s * SS::kStage);             // [column i][lane]
+    const T* at = reinterpret_cast<const T*>(smem + s * SS::kStage);             // [column i][row r][lane]
     const V2* cs = reinterpret_cast<const V2*>(smem + s * SS::kStage + SS::kAStage);  // [wave i][pair l]
     const int w0 = t * CB - 1;
     // Interior: every wave's rotations j = w-l, l < KR, lie in [0, n-2].
     if (k == KR && w0 - (KR - 1) >= 0 && w0 + CB - 1 <= n - 2)
-      stream_tile<T, KR, true>(win, at, cs, w0, k, n, rowok, arow, lda, lane);
+      stream_tile<T, KR, R, true>(win, at, cs, w0, k, n, rowok, arow, lda, lane);
     else
-      stream_tile<T, KR, false>(win, at, cs, w0, k, n, rowok, arow, lda, lane);
+      stream_tile<T, KR, R, false>(win, at, cs, w0, k, n, rowok, arow, lda, lane);
     __syncwarp();                                // every lane has read the stage
     if (lane == 0 && t + S < ntiles) issue(t + S);
   }

@@ -38,9 +38,10 @@ def bits(x):
     return x.view(np.uint64 if x.dtype == np.float64 else np.uint32)
 
 
-CASES = [  # m, n, k, lda slack
-    (32, 32, 1, 0), (33, 40, 2, 4), (64, 41, 3, 0), (100, 77, 4, 8), (95, 200, 5, 0),
-    (128, 33, 6, 4), (257, 130, 7, 0), (64, 300, 8, 12), (1000, 3000, 1, 0), (50, 1001, 8, 2),
+CASES = [  # m, n, k, lda slack (m < 64 or n < 32: the wavefront kernel)
+    (32, 32, 1, 0), (33, 40, 2, 4), (64, 32, 1, 0), (65, 40, 2, 4), (127, 41, 3, 0), (100, 77, 4, 8),
+    (95, 200, 5, 0), (128, 33, 6, 4), (257, 130, 7, 0), (64, 300, 8, 12), (1000, 3000, 1, 0),
+    (50, 1001, 8, 2), (300, 31, 2, 0),
 ]
 
 
