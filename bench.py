@@ -52,6 +52,20 @@ UNIT = "rot-rows/s"
 # kernel reads and writes A about once and its traffic grows with n.
 NCU_TRAFFIC = {"bytes": 1.0207e9, "kernel_src_sha": "89379a2d22527eb6"}
 
+# The same for the single-p-block column stream at k = 1 (FP32, 8192 x 8192),
+# captured on the full workload (the kernel takes 0.1 ms).
+NCU_TRAFFIC_STREAM = {"bytes": 4.7569e8, "kernel_src_sha": "ab7728a52e62bf50"}
+
+
+def stream_src_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("rs_stream.cuh", "rs_stream.cu", "rs_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2412_01852_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -640,7 +654,9 @@ def run_variant(args):
                                   "achieved": first["hbm_gbs"], "peak": hbm, "unit": "GB/s",
                                   "frac": first.get("frac_of_measured_hbm"),
                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)",
-                                  "algorithmic_bytes": first["bytes"]}})
+                                  "algorithmic_bytes": first["bytes"],
+                                  "traffic": NCU_TRAFFIC_STREAM["bytes"]
+                                  if NCU_TRAFFIC_STREAM["kernel_src_sha"] == stream_src_sha() else None}})
         print(json.dumps(line), flush=True)
         return
 
