@@ -615,7 +615,9 @@ def run_variant(args):
         rows = []
         A32 = _dev_colmajor(torch, A.astype(np.float32), dev)
         A64 = _dev_colmajor(torch, A, dev)
-        for prec, kk in (("f32", 1), ("f32", 2), ("f32", 4), ("f32", 8), ("f64", 1)):
+        # k > 8: the wavefront kernel (several p-blocks), for the crossover
+        for prec, kk in (("f32", 1), ("f32", 2), ("f32", 4), ("f32", 8), ("f32", 16), ("f32", 32), ("f32", 64),
+                         ("f64", 1), ("f64", 2), ("f64", 8), ("f64", 16), ("f64", 32)):
             C, S = wl.rotations(n, kk, cfg["seed"])
             if prec == "f32":
                 Cd, Sd = (_dev_colmajor(torch, X.astype(np.float32), dev) for X in (C, S))
@@ -625,17 +627,22 @@ def run_variant(args):
                 Cd, Sd = (_dev_colmajor(torch, X, dev) for X in (C, S))
                 fn = lambda: rs.rot_apply(A64, Cd, Sd)
                 esz, fpeak = 8, fp64_peak
+            reps = max(args.steps, 10)
             api.trace_start()
-            ms = timed_alone(fn, max(args.steps, 10))
+            ms = timed_alone(fn, reps)
             recs = api.trace_stop()
             kern = [r[1] for r in recs if r[0] == ("wave_f32" if prec == "f32" else "wave_f64")]
-            kms = float(np.median(kern)) if kern else ms
+            kms = sum(kern) / (3 + reps) if kern else ms       # every launch of a call (warm-up included)
             Wk = wl.rotation_rows(m, n, kk)
-            nbytes = 2 * m * n * esz + 2 * (n - 1) * kk * esz      # A read and written once, C and S read
+            # The column stream makes one pass over A per 8 sequences (FP32 up to
+            # k = 48, FP64 up to 16); the wavefront kernel one pass in all.
+            passes = -(-kk // 8) if kk <= (48 if prec == "f32" else 16) else 1
+            nbytes = passes * 2 * m * n * esz + 2 * (n - 1) * kk * esz   # A read and written per pass, C and S read
             # ms: the whole call (scratch, repack, kernel, status); kernel_ms: the
             # rotation kernel alone (CUDA events around its launch), which the
             # roofline fractions use.
-            row = {"precision": prec, "k": kk, "ms": ms, "kernel_ms": kms, "rot_rows_per_s": Wk / (ms * 1e-3),
+            row = {"precision": prec, "k": kk, "passes": passes, "ms": ms, "kernel_ms": kms,
+                   "rot_rows_per_s": Wk / (ms * 1e-3),
                    "tflops": 6.0 * Wk / (kms * 1e-3) / 1e12,
                    "frac_of_nominal_flops": 6.0 * Wk / (kms * 1e-3) / 1e12 / fpeak,
                    "hbm_gbs": nbytes / (kms * 1e-3) / 1e9, "bytes": nbytes}
@@ -646,7 +653,8 @@ def run_variant(args):
         first = rows[0]
         line.update({"value": first["rot_rows_per_s"], "ms_per_step": first["ms"], "dtype": "f32",
                      "config": {"workload": "small k: A 8192x8192 N(0,1) (FP32 and FP64), C/S 8191xk from uniform "
-                                            "angles, k in {1,2,4,8} (FP32) and 1 (FP64), seed 2",
+                                            "angles, k in {1,2,4,8,16,32,64} (FP32) and {1,2,8,16,32} (FP64), "
+                                            "seed 2",
                                 "m": m, "n": n, "l2": "flushed before every timed run (256 MiB write)"},
                      "per_k": rows,
                      "roofline": {"bound": "hbm", "kernel": "stream_kernel<float, 1> at k = 1",

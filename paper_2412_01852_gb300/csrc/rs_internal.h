@@ -40,7 +40,7 @@ template <typename T>
 rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
                       const T* S, int64_t lds, cudaStream_t stream, const WaveOptions& opt);
 
-// The single-p-block column stream (rs_stream.cu) for k <= 8: whether it
+// The column stream (rs_stream.cu), one pass per 8 sequences: whether it
 // takes this problem, and the call.
 template <typename T>
 bool stream_fits(int64_t m, int64_t n, int64_t k, const T* A, int64_t lda);

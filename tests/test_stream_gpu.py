@@ -1,9 +1,9 @@
-"""The single-p-block column stream (k <= 8) that rot_apply and rot_apply_f32
-take when A is TMA-addressable: bit-exact against the oracles on ragged
-shapes, padded leading dimensions, every k from 1 to 8 (so every window size
-and the k < window case), and the full 8192 x 8192 matrix at k = 1.  Leading
-dimensions the stream cannot address fall back to the wavefront kernel, with
-the same bits."""
+"""The column stream (one pass per 8 sequences) that rot_apply (k <= 16) and
+rot_apply_f32 (k <= 48) take when A is TMA-addressable: bit-exact against the
+oracles on ragged shapes, padded leading dimensions, every k from 1 to 8 (so
+every window size and the k < window case), several passes (k = 9, 16, 23,
+48), and the full 8192 x 8192 matrix at k = 1.  Leading dimensions the stream
+cannot address fall back to the wavefront kernel, with the same bits."""
 import numpy as np
 import pytest
 
@@ -41,7 +41,7 @@ def bits(x):
 CASES = [  # m, n, k, lda slack (m < 64 or n < 32: the wavefront kernel)
     (32, 32, 1, 0), (33, 40, 2, 4), (64, 32, 1, 0), (65, 40, 2, 4), (127, 41, 3, 0), (100, 77, 4, 8),
     (95, 200, 5, 0), (128, 33, 6, 4), (257, 130, 7, 0), (64, 300, 8, 12), (1000, 3000, 1, 0),
-    (50, 1001, 8, 2), (300, 31, 2, 0),
+    (50, 1001, 8, 2), (300, 31, 2, 0), (96, 100, 9, 0), (130, 257, 16, 4), (70, 90, 23, 0), (64, 200, 48, 8),
 ]
 
 
