@@ -17,11 +17,6 @@ namespace {
 
 inline int64_t round_up256(int64_t x) { return (x + 255) / 256 * 256; }
 
-// Rows per lane.  One (more warps: with a few warps per SM, each warp's issue
-// rate bounds the stream).
-template <typename T, int KR>
-constexpr int stream_rows() { return 1; }
-
 template <typename T, int KR>
 rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc, const T* S,
                          int64_t lds, cudaStream_t s) {

@@ -44,6 +44,11 @@ struct StreamShape {
   static constexpr int kSmem = S * kStage + S * 8;
 };
 
+// Rows per lane of the launch.  One (more warps: with a few warps per SM,
+// each warp's issue rate bounds the stream).
+template <typename T, int KR>
+constexpr int stream_rows() { return 1; }
+
 // One tile: CB waves.  FULL: every rotation of every wave exists (k == KR and
 // the tile lies inside the triangle-free part), so no predicates.
 template <typename T, int KR, int R, bool FULL>
