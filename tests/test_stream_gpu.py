@@ -42,6 +42,8 @@ CASES = [  # m, n, k, lda slack (m < 64 or n < 32: the wavefront kernel)
     (32, 32, 1, 0), (33, 40, 2, 4), (64, 32, 1, 0), (65, 40, 2, 4), (127, 41, 3, 0), (100, 77, 4, 8),
     (95, 200, 5, 0), (128, 33, 6, 4), (257, 130, 7, 0), (64, 300, 8, 12), (1000, 3000, 1, 0),
     (50, 1001, 8, 2), (300, 31, 2, 0), (96, 100, 9, 0), (130, 257, 16, 4), (70, 90, 23, 0), (64, 200, 48, 8),
+    # at the thresholds: no tile of all-complete waves (n = 64, k = 8), a single tile, one row past a strip
+    (64, 64, 8, 0), (64, 64, 1, 0), (65, 65, 3, 0), (64, 127, 5, 4), (97, 64, 2, 0),
 ]
 
 
