@@ -16,6 +16,7 @@ Functions and the passages they follow:
 * ``rot_sequence_inverse``    -- the transposed rotations in reverse order.
 * ``rot_sequence_block``      -- Algorithm 4 (rot_sequence_block).
 * ``form_block``              -- the accumulated orthogonal block of rs_gemm (Section 8).
+* ``form_block_f32``          -- the same block accumulated in single precision.
 * ``rot_sequence_gemm``       -- Algorithm 2 regrouped into accumulated blocks applied
                                  by FP64 matrix products (rs_gemm, Section 8).
 * ``refl_sequence``           -- 2x2 reflectors (tau, nu) in Algorithm 2's order (Section 6).
@@ -76,6 +77,9 @@ def _declare(lib):
     lib.oracle_form_block.argtypes = [_i64, _i64, _i64, _i64, _i64, _i64,
                                       _dp, _i64, _dp, _i64, _dp, _i64]
     lib.oracle_form_block.restype = None
+    lib.oracle_form_block_f32.argtypes = [_i64, _i64, _i64, _i64, _i64, _i64,
+                                          _dp, _i64, _dp, _i64, _fp, _i64]
+    lib.oracle_form_block_f32.restype = None
     return lib
 
 
@@ -230,6 +234,19 @@ def form_block(C, S, n, w0, nb, p0, kb):
     Q = np.zeros((L, L), dtype=np.float64, order="F")
     lib.oracle_form_block(n, k, w0, nb, p0, kb, _ptr(C, ctypes.c_double), max(1, n - 1),
                           _ptr(S, ctypes.c_double), max(1, n - 1), _ptr(Q, ctypes.c_double), L)
+    return Q
+
+
+def form_block_f32(C, S, n, w0, nb, p0, kb):
+    """``form_block`` in single precision: (c,s) rounded to FP32, FP32 rotations on the FP32 identity."""
+    lib = _load()
+    C = _fortran(C, np.float64)
+    S = _fortran(S, np.float64)
+    k = C.shape[1] if C.ndim == 2 else 0
+    L = nb + kb
+    Q = np.zeros((L, L), dtype=np.float32, order="F")
+    lib.oracle_form_block_f32(n, k, w0, nb, p0, kb, _ptr(C, ctypes.c_double), max(1, n - 1),
+                              _ptr(S, ctypes.c_double), max(1, n - 1), _ptr(Q, ctypes.c_float), L)
     return Q
 
 

@@ -177,6 +177,32 @@ void oracle_form_block(int64_t n, int64_t k,
 }
 
 /*
+ * The same accumulated block in single precision: each (c,s) is rounded to
+ * the nearest FP32 value and the block's rotations are applied to the FP32
+ * identity with rot_f32, in the order of oracle_form_block.
+ */
+void oracle_form_block_f32(int64_t n, int64_t k,
+                           int64_t w0, int64_t nb, int64_t p0, int64_t kb,
+                           const double *C, int64_t ldc,
+                           const double *S, int64_t lds,
+                           float *Q, int64_t ldq)
+{
+    int64_t L = nb + kb;
+    int64_t c0 = w0 - kb + 1;
+    for (int64_t jj = 0; jj < L; ++jj)
+        for (int64_t ii = 0; ii < L; ++ii)
+            Q[ii + jj * ldq] = (ii == jj) ? 1.0f : 0.0f;
+    for (int64_t p = p0; p < p0 + kb && p < k; ++p) {
+        for (int64_t j = 0; j + 1 < n; ++j) {
+            int64_t w = j + (p - p0);
+            if (w < w0 || w >= w0 + nb) continue;
+            int64_t col = j - c0;
+            rot_f32(L, Q + col * ldq, Q + (col + 1) * ldq, (float)C[j + p * ldc], (float)S[j + p * lds]);
+        }
+    }
+}
+
+/*
  * 2x2 reflectors in place of rotations (Section 6): the reflector (tau, nu)
  * is H = I - tau * v v^T with v = (1, nu)^T; applied to a row [x, y] it gives
  *     x' = x - tau*(x + nu*y),   y' = y - nu*tau*(x + nu*y),

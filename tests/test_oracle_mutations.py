@@ -31,6 +31,8 @@ PINS = [
     lambda: pins.test_p9_exact_rational_product_bound(3, 4, 3),
     pins.test_alg4_block_equals_alg2_with_identity_outside,
     lambda: pins.test_form_block_orthogonal_and_structured(40, 9, 8, 4, 16, 4),
+    lambda: pins.test_form_block_f32_within_rotation_error_of_f64(40, 9, 8, 4, 16, 4),
+    pins.test_form_block_f32_exact_for_signed_permutations,
     lambda: pins.test_gemm_regrouping_equals_rotations(5, 70, 20, 16, 8),
     pins.test_f32_within_stated_error_of_f64,
     pins.test_f32_exact_special_case,
@@ -63,6 +65,12 @@ MUTANTS = [
      "for (int64_t j = kk - 1 - p; j < nn - p - 1; ++j)", 0),
     ("form_block_cs", "C[j + p * ldc], S[j + p * lds]);\n        }\n    }\n}",
      "S[j + p * lds], C[j + p * ldc]);\n        }\n    }\n}", 0),
+    ("form_block_f32_cs", "(float)C[j + p * ldc], (float)S[j + p * lds]",
+     "(float)S[j + p * lds], (float)C[j + p * ldc]", 0),
+    ("form_block_f32_window", "if (w < w0 || w >= w0 + nb) continue;",
+     "if (w < w0 || w >= w0 + nb - 1) continue;", 1),
+    ("form_block_f32_identity", "Q[ii + jj * ldq] = (ii == jj) ? 1.0f : 0.0f;",
+     "Q[ii + jj * ldq] = (ii + 1 == jj) ? 1.0f : 0.0f;", 0),
     ("f32_sign", "y[i] = fmaf(c, yi, -sx);", "y[i] = fmaf(c, yi, sx);", 0),
     ("refl_sign", "y[i] = fma(-nu, w, yi);", "y[i] = fma(nu, w, yi);", 0),
     ("refl_dropped", "double t = fma(nu, yi, xi);", "double t = xi;", 0),

@@ -261,6 +261,43 @@ def test_every_block_of_a_schedule_has_the_zero_triangle(n, k, nb, kb):
         assert np.all(jj >= ii - kb), (w0, p0)
 
 
+@pytest.mark.parametrize("n,k,nb,kb,w0,p0", [(40, 9, 8, 4, 16, 4), (40, 9, 8, 4, 32, 8),
+                                             (300, 64, 256, 64, 256, 0), (600, 130, 256, 64, 0, 128)])
+def test_form_block_f32_within_rotation_error_of_f64(n, k, nb, kb, w0, p0):
+    """The FP32 block against the FP64 one.  A block's rotations fall into
+    about L + 2kb sets of disjoint pairs (one per anti-diagonal j + 2p), and
+    each set perturbs a row by a few units of FP32 rounding (the rounded
+    (c,s) and the four operations), so every row stays within
+    6 (L + 2kb) u32 of the FP64 row; it is also orthogonal to that order and
+    keeps the zero triangle."""
+    C, S = wl.rotations(n, k, seed=42)
+    Q64 = oracle.form_block(C, S, n, w0, nb, p0, kb)
+    Q32 = oracle.form_block_f32(C, S, n, w0, nb, p0, kb)
+    L = nb + kb
+    assert Q32.dtype == np.float32 and Q32.shape == (L, L)
+    err = np.linalg.norm(Q32.astype(np.float64) - Q64, axis=1)
+    assert err.max() <= 6 * (L + 2 * kb) * U32
+    assert err.max() > 0                      # it did round
+    Qd = Q32.astype(np.float64)
+    assert np.abs(Qd.T @ Qd - np.eye(L)).max() <= 12 * (L + 2 * kb) * U32
+    ii, jj = np.nonzero(Q32)
+    assert np.all(jj >= ii - kb)
+
+
+def test_form_block_f32_exact_for_signed_permutations():
+    """With c, s in {0, +-1} every operation is exact in any precision, so the
+    FP32 block equals the FP64 one entry for entry."""
+    n, k, nb, kb = 70, 12, 16, 8
+    rng = _rng(43)
+    pick = rng.integers(0, 4, size=(n - 1, k))
+    C = np.choose(pick, [1.0, 0.0, 0.0, -1.0])
+    S = np.choose(pick, [0.0, 1.0, -1.0, 0.0])
+    for w0, p0 in oracle.block_schedule(n, k, nb, kb):
+        Q64 = oracle.form_block(C, S, n, w0, nb, p0, kb)
+        Q32 = oracle.form_block_f32(C, S, n, w0, nb, p0, kb)
+        assert np.array_equal(Q32.astype(np.float64), Q64), (w0, p0)
+
+
 @pytest.mark.parametrize("m,n,k,nb,kb", [(9, 40, 9, 8, 4), (5, 70, 20, 16, 8), (3, 12, 30, 4, 4),
                                          (16, 300, 64, 64, 16)])
 def test_gemm_regrouping_equals_rotations(m, n, k, nb, kb):
