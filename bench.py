@@ -257,8 +257,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-rows", type=int, default=512)
     ap.add_argument("--variant", default="plain",
-                    choices=["plain", "f32", "gemm-f16", "gemm-bf16", "gemm-dmma", "batched", "serving",
-                             "reflectors", "left", "small-k"],
+                    choices=["plain", "f32", "gemm-f16", "gemm-bf16", "gemm-dmma", "gemm-f16-q32",
+                             "gemm-bf16-q32", "batched", "serving", "reflectors", "left", "small-k"],
                     help="plain (default) is the measured line; the others measure the other "
                          "paths of the library on the same GPU")
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -480,7 +480,8 @@ def run_variant(args):
             cfg_line = {"workload": "precision-8192 FP32: A 8192x8192, C/S 8191x192 rounded to FP32", "m": m,
                         "n": n, "k": k}
         else:
-            mode = args.variant.split("-")[1]
+            mode = args.variant[len("gemm-"):]          # dmma, f16, bf16, f16-q32, bf16-q32
+            base = mode.split("-")[0]
             nb, kb = cfg["nb"], cfg["kb"]
             once = rs.colmajor(A64)
             api.rot_apply_gemm(once, C64, S64, nb=nb, kb=kb, mode=mode)
@@ -490,8 +491,8 @@ def run_variant(args):
             drift = _orth_drift(torch, lambda Q: api.rot_apply_gemm(Q, C64, S64, nb=nb, kb=kb, mode=mode), n,
                                 torch.float64, dev)
             drift_bound = {"dmma": 10 * n * 2.0 ** -53, "f16": 8 * k * 2.0 ** -24,
-                           "bf16": 8 * -(-k // kb) * 2.0 ** -16}[mode]
-            kind, peak, dtype = "form_blocks", fp64_peak, {"f16": "f16x2", "bf16": "bf16x2", "dmma": "f64"}[mode]
+                           "bf16": 8 * -(-k // kb) * 2.0 ** -16}[base]
+            kind, peak, dtype = "form_blocks", fp64_peak, {"f16": "f16x2", "bf16": "bf16x2", "dmma": "f64"}[base]
             cfg_line = {"workload": "precision-8192 accumulated blocks: A 8192x8192, k=192, nb=%d, kb=%d, %s"
                                     % (nb, kb, mode), "m": m, "n": n, "k": k, "nb": nb, "kb": kb, "mode": mode}
         torch.cuda.synchronize()
@@ -521,16 +522,25 @@ def run_variant(args):
             kms = kernels.get("form_blocks", 0.0)
             nblk = api.form_blocks_count(n, k, cfg["nb"], cfg["kb"])
             form_rows = nblk * (cfg["nb"] + cfg["kb"]) * cfg["nb"] * cfg["kb"]
-            line["roofline"] = {"bound": "alu", "kernel": "wave_batched_kernel (block formation, FP64)",
-                                "achieved": 6.0 * form_rows / (kms * 1e-3) / 1e12, "peak": fp64_peak,
+            q32 = cfg_line["mode"].endswith("-q32")
+            fpeak = fp32_peak if q32 else fp64_peak
+            line["roofline"] = {"bound": "alu",
+                                "kernel": "form32_kernel (block formation, FP32 lane pipeline)" if q32 else
+                                          "wave_batched_kernel (block formation, FP64)",
+                                "achieved": 6.0 * form_rows / (kms * 1e-3) / 1e12, "peak": fpeak,
                                 "unit": "TFLOP/s", "kernel_ms": kms,
+                                "peak_source": "nominal %s FMA rate: SMs x %d x 2 x max SM clock"
+                                               % (("FP32", FP32_FMA_PER_SM_CLK) if q32 else
+                                                  ("FP64", FP64_FMA_PER_SM_CLK)),
                                 "note": "achieved counts the rotations of all blocks on full identity rows "
-                                        "(zero waves are skipped, so this overstates executed flops)"}
-            line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
+                                        "(%s)" % ("the pipeline also runs (1,0) stages outside the block"
+                                                  if q32 else "zero waves are skipped, so this overstates "
+                                                              "executed flops")}
+            line["roofline"]["frac"] = line["roofline"]["achieved"] / fpeak
             # The block apply on its own: 2*L^2 flops per row and block per product.
             akms = kernels.get("gemm_apply", 0.0)
             L = cfg["nb"] + cfg["kb"]
-            mode = cfg_line["mode"]
+            mode = cfg_line["mode"].split("-")[0]
             products = 1 if mode == "dmma" else 3
             aflops = products * 2.0 * m * L * L * nblk
             if akms > 0:

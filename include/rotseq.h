@@ -166,7 +166,9 @@ rot_status rot_apply_noalloc(int64_t m, int64_t n, int64_t k, double* A, int64_t
 typedef enum {
   ROT_GEMM_F64_DMMA = 0,    /* FP64 tensor MMA, FP64 accumulation */
   ROT_GEMM_SPLIT_BF16 = 1,  /* A, Q split into BF16 hi+lo; hi*hi+hi*lo+lo*hi, FP32 accumulation */
-  ROT_GEMM_SPLIT_F16 = 2    /* FP16 hi + 2^-11*lo; hi*hi and hi*lo+lo*hi in two FP32 accumulators */
+  ROT_GEMM_SPLIT_F16 = 2,   /* FP16 hi + 2^-11*lo; hi*hi and hi*lo+lo*hi in two FP32 accumulators */
+  ROT_GEMM_SPLIT_BF16_Q32 = 3,  /* ROT_GEMM_SPLIT_BF16 with the blocks formed in FP32 (rot_form_blocks_f32) */
+  ROT_GEMM_SPLIT_F16_Q32 = 4    /* ROT_GEMM_SPLIT_F16 with the blocks formed in FP32 */
 } rot_gemm_mode;
 
 /* Number of accumulated blocks for (n, k, nb, kb): for each group of kb
@@ -192,6 +194,22 @@ rot_status rot_form_blocks(int64_t n, int64_t k, const double* C, int64_t ldc, c
                            int64_t lds, int nb, int kb, double* Q, void* stream);
 
 /*
+ * rot_form_blocks in single precision: each (c,s) rounded to the nearest
+ * FP32 value and the block's rotations applied to the FP32 identity with the
+ * same FMA placement in FP32 (x' = fmaf(c,x,RN(s*y)), y' = fmaf(c,y,-RN(s*x))).
+ * Entries equal that sequential FP32 computation exactly; only the sign of
+ * zero entries may differ.  Q receives rot_form_blocks_count() matrices of
+ * L x L floats (L = nb + kb), column-major, one after the other.  The
+ * rotations are run as a pipeline over a warp's lanes, each lane holding up
+ * to 4 sequences, so kb <= 128; otherwise the requirements of
+ * rot_form_blocks, and Q 16-byte aligned.  Scratch (a per-block (c,s)
+ * table) comes from the stream-ordered allocator.  ROT_EINVAL on bad
+ * arguments.  Asynchronous on `stream`.
+ */
+rot_status rot_form_blocks_f32(int64_t n, int64_t k, const double* C, int64_t ldc, const double* S,
+                               int64_t lds, int nb, int kb, float* Q, void* stream);
+
+/*
  * Algorithm 2's result computed the rs_gemm way: form the blocks
  * (rot_form_blocks, FP64), then update A block by block in the blocks' order,
  * A(:, c0:c0+L) <- A(:, c0:c0+L) * Q_b, with tensor-core matrix products of
@@ -202,8 +220,10 @@ rot_status rot_form_blocks(int64_t n, int64_t k, const double* C, int64_t ldc, c
  * memory.  Accuracy against the FP64 result: DMMA within 16*(k+nb+kb)*2^-53
  * per row; the split modes lose precision in the products (FP16 split:
  * per-row relative error below 8*k*2^-24; BF16 split: about 2^-16 per block
- * product).  Same arguments as rot_apply plus nb, kb (multiples of 16,
- * nb + kb <= 512) and the mode.  Scratch (the blocks and their split copies)
+ * product).  The *_Q32 modes form the blocks with rot_form_blocks_f32
+ * instead (kb <= 128), which adds FP32 rounding to the blocks (per-row
+ * error within the same bounds).  Same arguments as rot_apply plus nb, kb
+ * (multiples of 16, nb + kb <= 512) and the mode.  Scratch (the blocks and their split copies)
  * comes from the stream-ordered allocator.
  */
 rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,

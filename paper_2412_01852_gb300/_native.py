@@ -48,6 +48,7 @@ SIGNATURES = {
     "rot_batch_autotune": (ci, [ci, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]),
     "rot_form_blocks_count": (i64, [i64, i64, ci, ci]),
     "rot_form_blocks": (ci, [i64, i64, vp, i64, vp, i64, ci, ci, vp, vp]),
+    "rot_form_blocks_f32": (ci, [i64, i64, vp, i64, vp, i64, ci, ci, vp, vp]),
     "rot_apply_gemm": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, ci, ci, ci, vp]),
     "rot_apply_gemm_workspace_size": (ci, [i64, i64, i64, ci, ci, ci, ctypes.POINTER(sz)]),
     "rot_apply_gemm_ws": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, ci, ci, ci, vp, sz, vp]),
@@ -99,7 +100,7 @@ class TraceRecord(ctypes.Structure):
 
 
 KERNEL_KINDS = {1: "wave_f64", 2: "wave_f32", 3: "wave_batched", 4: "form_blocks", 5: "gemm_apply", 6: "reflect_f64"}
-GEMM_MODES = {"dmma": 0, "bf16": 1, "f16": 2}
+GEMM_MODES = {"dmma": 0, "bf16": 1, "f16": 2, "bf16-q32": 3, "f16-q32": 4}
 
 
 class RotError(RuntimeError):

@@ -359,6 +359,19 @@ def rot_form_blocks(n, C, S, nb, kb, stream=None):
     return Q[:nblk]
 
 
+def rot_form_blocks_f32(n, C, S, nb, kb, stream=None):
+    """All accumulated blocks formed in FP32: a (nblk, L, L) float32 tensor whose [b] is Q_b transposed."""
+    lib = _native.load()
+    k = C.shape[1]
+    nblk = form_blocks_count(n, k, nb, kb)
+    L = nb + kb
+    Q = torch.empty((max(nblk, 1), L, L), dtype=torch.float32, device=C.device)
+    _native.check(lib.rot_form_blocks_f32(int(n), int(k), _ptr(C), _ld(C, n - 1), _ptr(S), _ld(S, n - 1),
+                                          int(nb), int(kb), Q.data_ptr(), _stream_handle(stream)),
+                  "rot_form_blocks_f32")
+    return Q[:nblk]
+
+
 def rot_apply_gemm(A, C, S, nb=256, kb=64, mode="f16", stream=None):
     """Algorithm 2 via accumulated blocks and tensor-core products (mode: dmma, bf16, f16)."""
     lib = _native.load()

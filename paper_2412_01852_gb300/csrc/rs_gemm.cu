@@ -11,6 +11,10 @@
 // the identity start as unit vectors, which lets whole waves on zero columns
 // be skipped (values are unchanged; only the sign of zeros can differ).
 //
+// The split modes also come with blocks formed in FP32 (rs_form_f32.cu):
+// their products keep about 16 (BF16) or 22 (FP16) bits, so FP32 blocks,
+// formed on the FP32 pipe at 64 times GB300's FP64 rate, lose little.
+//
 // Block apply: the split modes run on the 5th-generation tensor cores
 // (tcgen05, TMEM accumulators; rs_gemm_tc.cu) for windows up to 320 columns.
 // FP64 DMMA, and wider windows, use mma.sync: one CTA per 32-row tile of A
@@ -28,6 +32,7 @@
 #include <cuda_bf16.h>
 
 #include "rs_batch.h"
+#include "rs_form_f32.h"
 #include "rs_gemm_tc.h"
 
 namespace rs {
@@ -72,21 +77,23 @@ __global__ void identity_kernel(double* Q, int L, int Lp, long long nblk) {
   }
 }
 
-// Split Q into hi/lo halves of the mode's 16-bit type (same column-major layout).
-template <int MODE>
-__global__ void split_kernel(const double* __restrict__ Q, uint16_t* __restrict__ hi,
+// Split Q (FP64 or FP32 blocks) into hi/lo halves of the mode's 16-bit type
+// (same column-major layout).  From an FP32 block, q - hi is exact in FP32,
+// so both give the halves of the same value the same way.
+template <int MODE, typename TQ>
+__global__ void split_kernel(const TQ* __restrict__ Q, uint16_t* __restrict__ hi,
                              uint16_t* __restrict__ lo, long long total) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const double q = Q[e];
+    const TQ q = Q[e];
     if (MODE == ROT_GEMM_SPLIT_BF16) {
       const __nv_bfloat16 h = __float2bfloat16_rn((float)q);
-      const __nv_bfloat16 l = __float2bfloat16_rn((float)(q - (double)__bfloat162float(h)));
+      const __nv_bfloat16 l = __float2bfloat16_rn((float)(q - (TQ)__bfloat162float(h)));
       hi[e] = __bfloat16_as_ushort(h);
       lo[e] = __bfloat16_as_ushort(l);
     } else {
       const __half h = __float2half_rn((float)q);
-      const __half l = __float2half_rn((float)((q - (double)__half2float(h)) * 2048.0));
+      const __half l = __float2half_rn((float)((q - (TQ)__half2float(h)) * (TQ)2048));
       hi[e] = __half_as_ushort(h);
       lo[e] = __half_as_ushort(l);
     }
@@ -642,23 +649,47 @@ static rot_status validate_gemm(int64_t m, int64_t n, int64_t k, const void* A, 
 
 namespace rs {
 
-// Workspace of one rs_gemm call: the formation layout, the FP64 blocks, their
-// split copies and a status word, at fixed offsets from a 256-byte aligned base.
+// The modes: their product arithmetic, and whether the blocks are formed in FP32.
+static bool mode_known(int mode) { return mode >= ROT_GEMM_F64_DMMA && mode <= ROT_GEMM_SPLIT_F16_Q32; }
+static bool mode_q32(int mode) { return mode == ROT_GEMM_SPLIT_BF16_Q32 || mode == ROT_GEMM_SPLIT_F16_Q32; }
+static int mode_split(int mode) {
+  if (mode == ROT_GEMM_SPLIT_BF16_Q32) return ROT_GEMM_SPLIT_BF16;
+  if (mode == ROT_GEMM_SPLIT_F16_Q32) return ROT_GEMM_SPLIT_F16;
+  return mode;
+}
+static bool mode_ok(int mode, int kb) { return mode_known(mode) && (!mode_q32(mode) || kb <= kForm32MaxKb); }
+
+// Workspace of one rs_gemm call: the formation layout, the blocks (FP64, or
+// FP32 for the *_Q32 modes), their split copies and a status word, at fixed
+// offsets from a 256-byte aligned base.
 struct GemmLayout {
-  FormLayout F;
+  FormLayout F;           // FP64 formation
+  Form32Layout F32;       // FP32 formation
+  bool q32 = false;
   int L = 0, Lp = 0;
   int64_t nblk = 0;
   size_t o_q = 0, o_hi = 0, o_lo = 0, o_status = 0, total = 0;
 };
 
 static void gemm_layout(int64_t n, int64_t k, int nb, int kb, rot_gemm_mode mode, GemmLayout* G) {
-  form_layout(n, k, nb, kb, &G->F);
   G->L = nb + kb;
   G->Lp = (int)round_up(G->L, 32);
-  G->nblk = (int64_t)G->F.blocks.size();
-  const size_t q_bytes = (size_t)G->nblk * G->Lp * G->Lp * sizeof(double);
+  G->q32 = mode_q32(mode);
+  size_t head, q_elem;
+  if (G->q32) {
+    form32_layout(n, k, nb, kb, G->Lp, &G->F32);
+    G->nblk = G->F32.nblk;
+    head = G->F32.total;
+    q_elem = sizeof(float);
+  } else {
+    form_layout(n, k, nb, kb, &G->F);
+    G->nblk = (int64_t)G->F.blocks.size();
+    head = G->F.total;
+    q_elem = sizeof(double);
+  }
+  const size_t q_bytes = (size_t)G->nblk * G->Lp * G->Lp * q_elem;
   const size_t split_bytes = mode == ROT_GEMM_F64_DMMA ? 0 : (size_t)G->nblk * G->Lp * G->Lp * sizeof(uint16_t);
-  G->o_q = round_up((int64_t)G->F.total, 1024);
+  G->o_q = round_up((int64_t)head, 1024);
   G->o_hi = round_up((int64_t)(G->o_q + q_bytes), 1024);
   G->o_lo = round_up((int64_t)(G->o_hi + split_bytes), 1024);
   G->o_status = round_up((int64_t)(G->o_lo + split_bytes), 256);
@@ -669,25 +700,39 @@ static void gemm_layout(int64_t n, int64_t k, int nb, int kb, rot_gemm_mode mode
 static rot_status gemm_enqueue(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C,
                                int64_t ldc, const double* S, int64_t lds, int nb, int kb, rot_gemm_mode mode,
                                const GemmLayout& G, unsigned char* base, cudaStream_t s) {
-  const FormLayout& F = G.F;
   const int L = G.L, Lp = G.Lp;
   const int64_t nblk = G.nblk;
   const size_t o_hi = G.o_hi, o_lo = G.o_lo, o_status = G.o_status;
-  double* Q = reinterpret_cast<double*>(base + G.o_q);
-  rot_status st = form_blocks_enqueue(n, k, C, ldc, S, lds, nb, kb, F, base, Q, Lp, s);
+  const int smode = mode_split(mode);
+  double* Q = nullptr;
+  float* Q32 = nullptr;
+  const int* c0 = nullptr;
+  rot_status st;
+  if (G.q32) {
+    Q32 = reinterpret_cast<float*>(base + G.o_q);
+    st = form32_enqueue(n, k, C, ldc, S, lds, nb, kb, G.F32, base, Q32, s);
+    c0 = reinterpret_cast<const int*>(base + G.F32.o_c0);
+  } else {
+    Q = reinterpret_cast<double*>(base + G.o_q);
+    st = form_blocks_enqueue(n, k, C, ldc, S, lds, nb, kb, G.F, base, Q, Lp, s);
+    c0 = reinterpret_cast<const int*>(base + G.F.o_c0);
+  }
   if (st == ROT_OK) {
     ApplyParams P{};
     P.A = A; P.lda = lda; P.m = (int)m; P.n = (int)n; P.L = L; P.Lp = Lp; P.nblk = (int)nblk;
-    P.c0 = reinterpret_cast<const int*>(base + F.o_c0);
+    P.c0 = c0;
     P.Q = Q;
     P.Qhi = reinterpret_cast<const uint16_t*>(base + o_hi);
     P.Qlo = reinterpret_cast<const uint16_t*>(base + o_lo);
     const long long qe = (long long)nblk * Lp * Lp;
     cudaError_t e = cudaSuccess;
     const int tr = trace_begin(ROT_KERNEL_GEMM_APPLY, m * (n - 1) * k, s);
-    if (mode != ROT_GEMM_F64_DMMA && apply_tc_supported(L, Lp, nb, mode)) {
+    uint16_t* hi = const_cast<uint16_t*>(P.Qhi);
+    uint16_t* lo = const_cast<uint16_t*>(P.Qlo);
+    if (smode != ROT_GEMM_F64_DMMA && apply_tc_supported(L, Lp, nb, smode)) {
       // tcgen05: 64-row tiles, accumulator in tensor memory.
-      split_chunked(Q, const_cast<uint16_t*>(P.Qhi), const_cast<uint16_t*>(P.Qlo), Lp, nblk, mode, s);
+      if (G.q32) split_chunked(Q32, hi, lo, Lp, nblk, smode, s);
+      else split_chunked(Q, hi, lo, Lp, nblk, smode, s);
       TcApplyParams T{};
       T.A = A; T.lda = lda; T.m = (int)m; T.n = (int)n; T.L = L; T.Lp = Lp; T.nb = nb;
       T.nblk = (int)nblk;
@@ -699,18 +744,18 @@ static rot_status gemm_enqueue(int64_t m, int64_t n, int64_t k, double* A, int64
       T.tmem_cols = cols;
       T.status = reinterpret_cast<int*>(base + o_status);
       e = cudaMemsetAsync(T.status, 0, sizeof(int), s);
-      if (e == cudaSuccess) e = launch_apply_tc(T, mode, s);
+      if (e == cudaSuccess) e = launch_apply_tc(T, smode, s);
       if (e == cudaSuccess) {
         record_status_async(T.status, s);
         count_launches(1);
       }
-    } else if (mode == ROT_GEMM_SPLIT_BF16) {
-      split_kernel<ROT_GEMM_SPLIT_BF16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
-                                                                  const_cast<uint16_t*>(P.Qlo), qe);
+    } else if (smode == ROT_GEMM_SPLIT_BF16) {
+      if (G.q32) split_kernel<ROT_GEMM_SPLIT_BF16, float><<<1024, 256, 0, s>>>(Q32, hi, lo, qe);
+      else split_kernel<ROT_GEMM_SPLIT_BF16, double><<<1024, 256, 0, s>>>(Q, hi, lo, qe);
       e = launch_apply<ROT_GEMM_SPLIT_BF16>(P, s);
-    } else if (mode == ROT_GEMM_SPLIT_F16) {
-      split_kernel<ROT_GEMM_SPLIT_F16><<<1024, 256, 0, s>>>(Q, const_cast<uint16_t*>(P.Qhi),
-                                                                 const_cast<uint16_t*>(P.Qlo), qe);
+    } else if (smode == ROT_GEMM_SPLIT_F16) {
+      if (G.q32) split_kernel<ROT_GEMM_SPLIT_F16, float><<<1024, 256, 0, s>>>(Q32, hi, lo, qe);
+      else split_kernel<ROT_GEMM_SPLIT_F16, double><<<1024, 256, 0, s>>>(Q, hi, lo, qe);
       e = launch_apply<ROT_GEMM_SPLIT_F16>(P, s);
     } else {
       e = launch_apply<ROT_GEMM_F64_DMMA>(P, s);
@@ -749,6 +794,23 @@ rot_status rot_form_blocks(int64_t n, int64_t k, const double* C, int64_t ldc, c
   return st;
 }
 
+rot_status rot_form_blocks_f32(int64_t n, int64_t k, const double* C, int64_t ldc, const double* S, int64_t lds,
+                               int nb, int kb, float* Q, void* stream) {
+  bool quick;
+  const void* dummy = reinterpret_cast<const void*>(0x100);
+  rot_status v = rs::validate_gemm(1, n, k, dummy, 1, C, ldc, S, lds, nb, kb, &quick);
+  if (v != ROT_OK || quick) return v;
+  if (!Q || kb > rs::kForm32MaxKb || (reinterpret_cast<uintptr_t>(Q) & 15u)) return ROT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rs::Form32Layout F;
+  rs::form32_layout(n, k, nb, kb, nb + kb, &F);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, F.total, s) != cudaSuccess) { cudaGetLastError(); return ROT_ENOMEM; }
+  rot_status st = rs::form32_enqueue(n, k, C, ldc, S, lds, nb, kb, F, static_cast<unsigned char*>(ws), Q, s);
+  cudaFreeAsync(ws, s);
+  return st;
+}
+
 rot_status rot_apply_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int nb, int kb, rot_gemm_mode mode,
                                          size_t* bytes) {
   if (!bytes) return ROT_EINVAL;
@@ -758,7 +820,7 @@ rot_status rot_apply_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int nb
   rot_status v = rs::validate_gemm(m, n, k, dummy, std::max<int64_t>(1, m), dummy, std::max<int64_t>(1, n - 1),
                                    dummy, std::max<int64_t>(1, n - 1), nb, kb, &quick);
   if (v != ROT_OK || quick) return v;
-  if (mode != ROT_GEMM_F64_DMMA && mode != ROT_GEMM_SPLIT_BF16 && mode != ROT_GEMM_SPLIT_F16) return ROT_EINVAL;
+  if (!rs::mode_ok(mode, kb)) return ROT_EINVAL;
   rs::GemmLayout G;
   rs::gemm_layout(n, k, nb, kb, mode, &G);
   *bytes = G.total;
@@ -771,7 +833,7 @@ rot_status rot_apply_gemm_ws(int64_t m, int64_t n, int64_t k, double* A, int64_t
   bool quick;
   rot_status v = rs::validate_gemm(m, n, k, A, lda, C, ldc, S, lds, nb, kb, &quick);
   if (v != ROT_OK || quick) return v;
-  if (mode != ROT_GEMM_F64_DMMA && mode != ROT_GEMM_SPLIT_BF16 && mode != ROT_GEMM_SPLIT_F16) return ROT_EINVAL;
+  if (!rs::mode_ok(mode, kb)) return ROT_EINVAL;
   rs::GemmLayout G;
   rs::gemm_layout(n, k, nb, kb, mode, &G);
   if (!workspace || workspace_bytes < G.total || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return ROT_EINVAL;
@@ -785,7 +847,7 @@ rot_status rot_apply_gemm(int64_t m, int64_t n, int64_t k, double* A, int64_t ld
   bool quick;
   rot_status v = rs::validate_gemm(m, n, k, A, lda, C, ldc, S, lds, nb, kb, &quick);
   if (v != ROT_OK || quick) return v;
-  if (mode != ROT_GEMM_F64_DMMA && mode != ROT_GEMM_SPLIT_BF16 && mode != ROT_GEMM_SPLIT_F16) return ROT_EINVAL;
+  if (!rs::mode_ok(mode, kb)) return ROT_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   rs::GemmLayout G;
   rs::gemm_layout(n, k, nb, kb, mode, &G);

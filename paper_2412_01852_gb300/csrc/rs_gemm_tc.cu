@@ -124,12 +124,6 @@ __device__ __forceinline__ void fence_async_smem() {
 }
 
 // ---- splitting ------------------------------------------------------------------
-__device__ __forceinline__ void split_f64(double x, uint16_t& h, uint16_t& l) {
-  const __nv_bfloat16 hb = __float2bfloat16_rn((float)x);
-  const __nv_bfloat16 lb = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hb)));
-  h = __bfloat16_as_ushort(hb);
-  l = __bfloat16_as_ushort(lb);
-}
 // FP64 <-> FP32 by integer bit operations.  GB300's FP64 pipe (2 lanes per
 // clock per SM) would otherwise be this kernel's bottleneck: a conversion
 // instruction there costs as much as a DFMA.
@@ -640,7 +634,8 @@ cudaError_t launch_apply_tc(const TcApplyParams& P, int mode, cudaStream_t s) {
 //   FP16: the same per half h of the columns (N = Lp/2 of them): the piece of
 //         column n of the half is at ((((2b + h)*nk + kc)*2 + kg)*N + n)*8;
 //         x = hi + 2^-11 lo.
-__global__ void split_chunked_kernel(const double* __restrict__ Q, uint16_t* __restrict__ hi,
+template <typename TQ>
+__global__ void split_chunked_kernel(const TQ* __restrict__ Q, uint16_t* __restrict__ hi,
                                      uint16_t* __restrict__ lo, int Lp, int mode, long long total) {
   const int nk = Lp / kKChunk;
   const int W = mode == ROT_GEMM_SPLIT_BF16 ? Lp : Lp / 2;     // columns per staged chunk
@@ -663,15 +658,17 @@ __global__ void split_chunked_kernel(const double* __restrict__ Q, uint16_t* __r
       b = t >> 1;
       col = (int)(t & 1) * W + n;
     }
-    const double q = Q[(b * Lp + col) * Lp + kc * kKChunk + kg * 8 + kk];
+    const TQ q = Q[(b * Lp + col) * Lp + kc * kKChunk + kg * 8 + kk];
     if (mode == ROT_GEMM_SPLIT_BF16) {
-      uint16_t hv, lv;
-      split_f64(q, hv, lv);
-      hi[e] = hv;
-      lo[e] = lv;
+      // From an FP32 block, q - hi is exact in FP32: the same halves as the
+      // FP64 route gives for the same value.
+      const __nv_bfloat16 hb = __float2bfloat16_rn((float)q);
+      const __nv_bfloat16 lb = __float2bfloat16_rn((float)(q - (TQ)__bfloat162float(hb)));
+      hi[e] = __bfloat16_as_ushort(hb);
+      lo[e] = __bfloat16_as_ushort(lb);
     } else {
       const __half h = __float2half_rn((float)q);
-      const __half l = __float2half_rn((float)((q - (double)__half2float(h)) * 2048.0));
+      const __half l = __float2half_rn((float)((q - (TQ)__half2float(h)) * (TQ)2048));
       hi[e] = __half_as_ushort(h);
       lo[e] = __half_as_ushort(l);
     }
@@ -679,7 +676,11 @@ __global__ void split_chunked_kernel(const double* __restrict__ Q, uint16_t* __r
 }
 
 void split_chunked(const double* Q, uint16_t* hi, uint16_t* lo, int Lp, long long nblk, int mode, cudaStream_t s) {
-  split_chunked_kernel<<<1024, 256, 0, s>>>(Q, hi, lo, Lp, mode, nblk * Lp * Lp);
+  split_chunked_kernel<double><<<1024, 256, 0, s>>>(Q, hi, lo, Lp, mode, nblk * Lp * Lp);
+}
+
+void split_chunked(const float* Q, uint16_t* hi, uint16_t* lo, int Lp, long long nblk, int mode, cudaStream_t s) {
+  split_chunked_kernel<float><<<1024, 256, 0, s>>>(Q, hi, lo, Lp, mode, nblk * Lp * Lp);
 }
 
 }  // namespace rs

@@ -31,5 +31,7 @@ cudaError_t launch_apply_tc(const TcApplyParams& P, int mode, cudaStream_t s);
 // Split Q (nblk blocks of Lp x Lp FP64, column-major) into the BF16 hi/lo
 // operands of launch_apply_tc, in its staging order.
 void split_chunked(const double* Q, uint16_t* hi, uint16_t* lo, int Lp, long long nblk, int mode, cudaStream_t s);
+// The same from FP32 blocks.
+void split_chunked(const float* Q, uint16_t* hi, uint16_t* lo, int Lp, long long nblk, int mode, cudaStream_t s);
 
 }  // namespace rs

@@ -97,6 +97,18 @@ def test_tc_issue_probe_argument_checks_without_device(lib):
     assert lib.rot_measure_tc_issue(64, 160, 2, 100, None) == 1
 
 
+def test_form_blocks_f32_arguments_checked_on_the_host(lib):
+    """Bad arguments of rot_form_blocks_f32 are refused before any device call."""
+    assert lib.rot_form_blocks_f32(300, 40, P, 299, P, 299, 64, 16, None, None) == 1             # no Q
+    assert lib.rot_form_blocks_f32(300, 40, P, 299, P, 299, 64, 16, ctypes.c_void_p(0x1004), None) == 1
+    assert lib.rot_form_blocks_f32(300, 200, P, 299, P, 299, 16, 144, P, None) == 1             # kb > 128
+    assert lib.rot_form_blocks_f32(300, 40, P, 299, P, 299, 60, 16, P, None) == 1               # nb % 16
+    assert lib.rot_form_blocks_f32(300, 40, P, 10, P, 299, 64, 16, P, None) == 1                # ldc
+    assert lib.rot_form_blocks_f32(1, 40, P, 1, P, 1, 64, 16, P, None) == 0                     # no blocks
+    assert lib.rot_form_blocks_count(300, 40, 64, 16) == len(
+        [(w0, p0) for p0 in range(0, 40, 16) for w0 in range(0, 299 + min(16, 40 - p0) - 1, 64)])
+
+
 def test_workspace_size_queries_are_host_only(lib):
     """Workspace sizes for the caller-owned-scratch entry points need no device."""
     sz = ctypes.c_size_t(0)
@@ -110,6 +122,14 @@ def test_workspace_size_queries_are_host_only(lib):
     assert lib.rot_apply_gemm_workspace_size(0, 300, 40, 64, 16, 1, ctypes.byref(sz)) == 0 and sz.value == 0
     assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 60, 16, 1, ctypes.byref(sz)) == 1   # nb % 16
     assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 64, 16, 7, ctypes.byref(sz)) == 1   # mode
+    assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 64, 16, 5, ctypes.byref(sz)) == 1   # mode
+    # FP32-formed blocks: FP32 blocks plus a (c,s) table instead of the FP64 blocks
+    assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 64, 16, 3, ctypes.byref(sz)) == 0
+    assert 0 < sz.value < small
+    assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 64, 16, 4, ctypes.byref(sz)) == 0 and sz.value > 0
+    assert lib.rot_apply_gemm_workspace_size(100, 600, 200, 16, 128, 3, ctypes.byref(sz)) == 0
+    assert lib.rot_apply_gemm_workspace_size(100, 600, 200, 16, 144, 3, ctypes.byref(sz)) == 1  # kb > 128
+    assert lib.rot_apply_gemm_workspace_size(100, 600, 200, 16, 144, 1, ctypes.byref(sz)) == 0
     assert lib.rot_apply_gemm_workspace_size(100, 300, 40, 64, 16, 1, None) == 1
     # a too-small or misaligned caller workspace is refused before any device call
     assert lib.rot_apply_gemm_ws(100, 300, 40, P, 100, P, 299, P, 299, 64, 16, 1, P, 16, None) == 1

@@ -8,6 +8,9 @@ FP64 oracle, per row:
   DMMA        16*(k+nb+kb)*2^-53
   split FP16  8*k*2^-24
   split BF16  4*ceil(k/kb)*2^-16   (two block products per element per p-block)
+The *-q32 modes form the blocks in FP32 (rot_form_blocks_f32), which equal
+the oracle's FP32 blocks entry for entry; their products are held to the
+same bounds.
 """
 import math
 
@@ -42,6 +45,7 @@ def row_rel(out, ref):
 
 
 def bound(mode, k, nb, kb):
+    mode = mode.split("-")[0]
     if mode == "dmma":
         return 16 * (k + nb + kb) * U64
     if mode == "f16":
@@ -67,7 +71,34 @@ def test_form_blocks_match_oracle(api, n, k, nb, kb):
         assert np.array_equal(got[nz].view(np.uint64), ref[nz].view(np.uint64)), b
 
 
-@pytest.mark.parametrize("mode", ["dmma", "f16", "bf16"])
+@pytest.mark.parametrize("n,k,nb,kb", [(40, 9, 16, 16), (100, 40, 32, 16), (300, 64, 64, 32),
+                                       (70, 100, 48, 16), (600, 130, 256, 64), (200, 50, 16, 48),
+                                       (300, 70, 64, 96), (150, 40, 32, 128), (2, 3, 16, 64)])
+def test_form_blocks_f32_match_oracle(api, n, k, nb, kb):
+    """FP32 blocks from the lane pipeline equal the oracle's sequential FP32
+    blocks entry for entry (non-zero entries bit for bit)."""
+    C, S = wl.rotations(n, k, seed=n + k + 5)
+    Q = api.rot_form_blocks_f32(n, dev(C), dev(S), nb, kb)
+    torch.cuda.synchronize()
+    api.rot_device_status()
+    sched = oracle.block_schedule(n, k, nb, kb)
+    assert Q.shape[0] == len(sched) and Q.dtype == torch.float32
+    Qh = Q.cpu().numpy()
+    for b, (w0, p0) in enumerate(sched):
+        ref = oracle.form_block_f32(C, S, n, w0, nb, p0, kb)
+        got = Qh[b].T
+        assert np.array_equal(got, ref), b
+        nz = ref != 0
+        assert np.array_equal(got[nz].view(np.uint32), ref[nz].view(np.uint32)), b
+
+
+def test_form_blocks_f32_rejects_kb_over_128(api):
+    C, S = wl.rotations(300, 200, seed=1)
+    with pytest.raises(Exception):
+        api.rot_form_blocks_f32(300, dev(C), dev(S), 16, 144)
+
+
+@pytest.mark.parametrize("mode", ["dmma", "f16", "bf16", "f16-q32", "bf16-q32"])
 @pytest.mark.parametrize("m,n,k,nb,kb", [(100, 300, 40, 64, 16), (33, 130, 70, 32, 32),
                                          (257, 500, 64, 256, 64), (64, 40, 100, 16, 16),
                                          (90, 200, 50, 16, 48)])
@@ -86,7 +117,7 @@ def test_apply_gemm_within_bound(api, mode, m, n, k, nb, kb):
         assert np.max(np.abs(out - viaq)) <= 16 * (nb + kb) * U64 * np.abs(A).max() * 4
 
 
-@pytest.mark.parametrize("mode", ["f16", "bf16"])
+@pytest.mark.parametrize("mode", ["f16", "bf16", "f16-q32", "bf16-q32"])
 def test_wide_window_split_modes(api, mode):
     """Windows wider than the tensor-memory kernel takes (nb + kb = 384) run
     on the mma.sync kernel; same bound."""
@@ -101,7 +132,7 @@ def test_wide_window_split_modes(api, mode):
     assert rel.max() <= bound(mode, k, nb, kb), rel.max()
 
 
-@pytest.mark.parametrize("mode", ["dmma", "f16", "bf16"])
+@pytest.mark.parametrize("mode", ["dmma", "f16", "bf16", "f16-q32", "bf16-q32"])
 def test_orthogonality_drift_on_identity(api, mode):
     n, k, nb, kb = 256, 48, 64, 16
     C, S = wl.rotations(n, k, seed=3)
@@ -110,11 +141,12 @@ def test_orthogonality_drift_on_identity(api, mode):
     torch.cuda.synchronize()
     Q = Ad.cpu().numpy()
     drift = np.abs(Q.T @ Q - np.eye(n)).max()
-    tol = {"dmma": 10 * n * U64, "f16": 8 * k * U32, "bf16": 8 * math.ceil(k / kb) * 2.0 ** -16}[mode]
+    tol = {"dmma": 10 * n * U64, "f16": 8 * k * U32,
+           "bf16": 8 * math.ceil(k / kb) * 2.0 ** -16}[mode.split("-")[0]]
     assert drift <= tol, drift
 
 
-@pytest.mark.parametrize("mode", ["f16", "bf16", "dmma"])
+@pytest.mark.parametrize("mode", ["f16", "bf16", "dmma", "f16-q32", "bf16-q32"])
 def test_precision_config_8192_sampled_rows(api, mode):
     """A 8192 x 8192, k = 192, nb = 256, kb = 64: rows sampled against the FP64 oracle."""
     cfg = wl.WORKLOADS["precision-8192"]
@@ -131,7 +163,7 @@ def test_precision_config_8192_sampled_rows(api, mode):
     assert row_rel(out, ref).max() <= bound(mode, k, nb, kb)
 
 
-@pytest.mark.parametrize("mode", ["bf16", "f16", "dmma"])
+@pytest.mark.parametrize("mode", ["bf16", "f16", "dmma", "bf16-q32", "f16-q32"])
 def test_caller_workspace_gives_the_same_bits(api, mode):
     """rot_apply_gemm_ws with caller-owned scratch equals rot_apply_gemm bit for bit."""
     m, n, k, nb, kb = 100, 300, 40, 64, 16
