@@ -513,9 +513,12 @@ def run_variant(args):
                                                 "input": "I_%d" % n},
                      "kernel_ms_per_step": per_step})
         if args.variant == "f32":
-            kms = kernels["wave_f32"]
+            # k = 192 runs as one pass of the lane pipeline; other shapes may
+            # add the wavefront kernel or the column stream.
+            kms = sum(per_step.get(kn, 0.0) for kn in ("pipe_f32", "wave_f32"))
+            kname = "+".join(kn for kn in ("pipe_f32_kernel", "wave_f32_kernel") if per_step.get(kn[:-7], 0.0) > 0)
             line["roofline"] = {"bound": "alu", "achieved": 6.0 * W / (kms * 1e-3) / 1e12, "peak": peak,
-                                "unit": "TFLOP/s", "kernel": "wave_kernel<float>", "kernel_ms": kms,
+                                "unit": "TFLOP/s", "kernel": kname, "kernel_ms": kms,
                                 "peak_source": "nominal FP32 FMA rate: SMs x 128 x 2 x max SM clock"}
             line["roofline"]["frac"] = line["roofline"]["achieved"] / peak
         else:
@@ -641,12 +644,18 @@ def run_variant(args):
             api.trace_start()
             ms = timed_alone(fn, reps)
             recs = api.trace_stop()
-            kern = [r[1] for r in recs if r[0] == ("wave_f32" if prec == "f32" else "wave_f64")]
+            kern = [r[1] for r in recs if r[0] in (("wave_f32", "pipe_f32") if prec == "f32" else ("wave_f64",))]
             kms = sum(kern) / (3 + reps) if kern else ms       # every launch of a call (warm-up included)
             Wk = wl.rotation_rows(m, n, kk)
             # The column stream makes one pass over A per 8 sequences (FP32 up to
-            # k = 48, FP64 up to 16); the wavefront kernel one pass in all.
-            passes = -(-kk // 8) if kk <= (48 if prec == "f32" else 16) else 1
+            # k = 48, FP64 up to 16), the FP32 lane pipeline one per 192 (plus
+            # the k mod 32 left over), the wavefront kernel one in all.
+            if kk <= (48 if prec == "f32" else 16):
+                passes = -(-kk // 8)
+            elif prec == "f32":
+                passes = -(-(kk // 32) // 6) + (-(-(kk % 32) // 8) if kk % 32 else 0)
+            else:
+                passes = 1
             nbytes = passes * 2 * m * n * esz + 2 * (n - 1) * kk * esz   # A read and written per pass, C and S read
             # ms: the whole call (scratch, repack, kernel, status); kernel_ms: the
             # rotation kernel alone (CUDA events around its launch), which the

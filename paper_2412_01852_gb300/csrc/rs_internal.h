@@ -48,6 +48,12 @@ template <typename T>
 rot_status stream_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
                         const T* S, int64_t lds, cudaStream_t stream);
 
+// FP32 rotations as a pipeline of sequences across a warp's lanes
+// (rs_pipe_f32.cu): whether it takes this problem, and the call.
+bool pipe_f32_fits(int64_t m, int64_t n, int64_t k);
+rot_status pipe_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C, int64_t ldc,
+                          const float* S, int64_t lds, cudaStream_t stream);
+
 bool encode_tile_map_2d(CUtensorMap* map, const void* base, bool is_double, uint64_t inner,
                         uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
                         uint32_t box_outer);
