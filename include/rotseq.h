@@ -428,7 +428,8 @@ enum {
   ROT_KERNEL_FORM_BLOCKS = 4,
   ROT_KERNEL_GEMM_APPLY = 5,
   ROT_KERNEL_REFLECT_F64 = 6,
-  ROT_KERNEL_PIPE_F32 = 7     /* FP32 sequences pipelined across a warp's lanes */
+  ROT_KERNEL_PIPE_F32 = 7,    /* FP32 sequences pipelined across a warp's lanes */
+  ROT_KERNEL_PIPE_F64 = 8     /* FP64 sequences pipelined across a warp's lanes */
 };
 
 /* Start recording a CUDA event pair around every main kernel the library

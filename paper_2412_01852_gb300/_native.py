@@ -100,7 +100,7 @@ class TraceRecord(ctypes.Structure):
 
 
 KERNEL_KINDS = {1: "wave_f64", 2: "wave_f32", 3: "wave_batched", 4: "form_blocks", 5: "gemm_apply", 6: "reflect_f64",
-                7: "pipe_f32"}
+                7: "pipe_f32", 8: "pipe_f64"}
 GEMM_MODES = {"dmma": 0, "bf16": 1, "f16": 2, "bf16-q32": 3, "f16-q32": 4}
 
 

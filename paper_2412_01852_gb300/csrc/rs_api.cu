@@ -49,10 +49,7 @@ rot_status rot_apply(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, co
   bool quick;
   rot_status v = validate(m, n, k, A, lda, C, ldc, S, lds, &quick);
   if (v != ROT_OK || quick) return v;
-  if (rs::stream_fits<double>(m, n, k, A, lda))
-    return rs::stream_apply<double>(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream));
-  return rs::wave_apply<double>(m, n, k, A, lda, C, ldc, S, lds,
-                                static_cast<cudaStream_t>(stream), rs::WaveOptions{});
+  return rs::apply_f64(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream));
 }
 
 rot_status rot_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C,

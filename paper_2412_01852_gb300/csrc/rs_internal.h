@@ -48,11 +48,20 @@ template <typename T>
 rot_status stream_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
                         const T* S, int64_t lds, cudaStream_t stream);
 
-// FP32 rotations as a pipeline of sequences across a warp's lanes
-// (rs_pipe_f32.cu): whether it takes this problem, and the call.
+// Rotations as a pipeline of sequences across a warp's lanes (rs_pipe.cu):
+// whether it takes this problem, and the call (FP32: k >= 32; FP64:
+// 3 <= k <= 32).
 bool pipe_f32_fits(int64_t m, int64_t n, int64_t k);
 rot_status pipe_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C, int64_t ldc,
                           const float* S, int64_t lds, cudaStream_t stream);
+bool pipe_f64_fits(int64_t m, int64_t n, int64_t k);
+// rot_apply's choice of FP64 kernel (also rot_apply_left's, on the
+// transpose): the lane pipeline for 3 <= k <= 32, the column stream for
+// fewer sequences, the wavefront kernel otherwise.
+rot_status apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C, int64_t ldc,
+                     const double* S, int64_t lds, cudaStream_t stream);
+rot_status pipe_apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C, int64_t ldc,
+                          const double* S, int64_t lds, cudaStream_t stream);
 
 bool encode_tile_map_2d(CUtensorMap* map, const void* base, bool is_double, uint64_t inner,
                         uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,

@@ -66,9 +66,7 @@ extern "C" rot_status rot_apply_left(int64_t m, int64_t n, int64_t k, double* A,
   do {
     e = rs::transpose(A, lda, B, n, m, n, s);
     if (e != cudaSuccess) { st = rs::cuda_failed(e, "rot_apply_left: transpose"); break; }
-    // The same dispatch as rot_apply (column stream for few sequences).
-    if (rs::stream_fits<double>(n, m, k, B, n)) st = rs::stream_apply<double>(n, m, k, B, n, C, ldc, S, lds, s);
-    else st = rs::wave_apply<double>(n, m, k, B, n, C, ldc, S, lds, s, rs::WaveOptions{});
+    st = rs::apply_f64(n, m, k, B, n, C, ldc, S, lds, s);     // the same dispatch as rot_apply
     if (st != ROT_OK) break;
     e = rs::transpose(B, n, A, lda, n, m, s);
     if (e != cudaSuccess) { st = rs::cuda_failed(e, "rot_apply_left: transpose back"); break; }

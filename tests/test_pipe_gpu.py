@@ -1,10 +1,15 @@
-"""The FP32 lane pipeline (rs_pipe_f32.cu) that rot_apply_f32 takes for
-k >= 32 and n >= 1024 (where the column stream does not): bit-exact against
+"""The lane pipeline (rs_pipe.cu).  FP32: rot_apply_f32 takes it for k >= 32
+and n >= 1024 (where the column stream does not); FP64: rot_apply (and
+rot_apply_left) for 3 <= k <= 32 and n >= 256.  FP32 cases: bit-exact against
 the FP32 oracle on ragged row counts, padded leading dimensions, every pass
 width (32 .. 192 sequences), several passes (k = 224, 384, 448), the k mod 32
 sequences left over (on the column stream or the wavefront kernel), signed
 zeros and infinities at the two ends of the column stream (where stages pass
-values through), and the full 8192 x 8192 matrix at k = 64 on sampled rows."""
+values through), and the full 8192 x 8192 matrix at k = 64 on sampled rows.
+FP64 cases: every group width (4, 8, 16, 32 lanes), k not a power of two
+(stages past k pass values through), ragged rows, padded leading dimensions,
+signed zeros and infinities, and 8192 x 8192 at k = 8 and 16 on sampled
+rows, bit-exact against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -58,6 +63,56 @@ def test_pipe_f32_bit_exact(rs, m, n, k, slack):
     out = buf.cpu().numpy()
     assert np.array_equal(bits(out[:m, :n]), bits(ref))
     assert np.all(np.isnan(out[m:, :n]))                      # rows past m untouched
+
+
+CASES64 = [  # m, n, k, lda slack: FP64, 3 <= k <= 32, n >= 256 (groups of 4, 8, 16 or 32 lanes)
+    (8, 256, 3, 0), (9, 300, 4, 1), (33, 700, 5, 0), (100, 1024, 8, 3), (17, 257, 9, 0), (64, 1000, 16, 2),
+    (5, 400, 17, 0), (71, 600, 31, 0), (40, 1100, 32, 1), (1, 256, 8, 0), (200, 333, 12, 0),
+]
+
+
+@pytest.mark.parametrize("m,n,k,slack", CASES64)
+def test_pipe_f64_bit_exact(rs, m, n, k, slack):
+    A, C, S = wl.problem(m, n, k, seed=m + 5 * n + k)
+    ref = oracle.rot_sequence(A, C, S)
+    Ad, buf = dev(A, m + slack)
+    rs.rot_apply(Ad, dev(C)[0], dev(S)[0])
+    rs.rot_device_status()
+    out = buf.cpu().numpy()
+    assert np.array_equal(out[:m, :n].view(np.uint64), ref.view(np.uint64))
+    assert np.all(np.isnan(out[m:, :n]))
+
+
+def test_pipe_f64_signed_zeros_and_infinities(rs):
+    m, n, k = 24, 500, 8
+    A, C, S = wl.problem(m, n, k, seed=92)
+    A[0, 0] = -0.0
+    A[1, n - 1] = -0.0
+    A[2, 3] = np.inf
+    A[9, n - 1] = -np.inf
+    A[11, :] = 0.0
+    A[12, :] = -0.0
+    ref = oracle.rot_sequence(A, C, S)
+    Ad, _ = dev(A)
+    rs.rot_apply(Ad, dev(C)[0], dev(S)[0])
+    rs.rot_device_status()
+    out = Ad.cpu().numpy()
+    nan = np.isnan(ref)
+    assert nan.any() and np.array_equal(np.isnan(out), nan)
+    assert np.array_equal(out[~nan].view(np.uint64), ref[~nan].view(np.uint64))
+
+
+@pytest.mark.parametrize("k", [8, 16])
+def test_pipe_f64_full_8192_sampled_rows(rs, k):
+    m = n = 8192
+    A, C, S = wl.problem(m, n, k, seed=6 + k)
+    rows = np.unique(np.concatenate([[0, 1, 7, 8, m - 1], np.random.default_rng(k).choice(m, 12, replace=False)]))
+    ref = oracle.rot_sequence(A[rows], C, S)
+    Ad, _ = dev(A)
+    rs.rot_apply(Ad, dev(C)[0], dev(S)[0])
+    rs.rot_device_status()
+    out = Ad[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
 
 
 def test_pipe_f32_signed_zeros_and_infinities(rs):

@@ -1,5 +1,6 @@
-"""The column stream (one pass per 8 sequences) that rot_apply (k <= 16) and
-rot_apply_f32 (k <= 48) take when A is TMA-addressable: bit-exact against the
+"""The column stream (one pass per 8 sequences) that rot_apply (k <= 16; the
+lane pipeline takes 3 <= k <= 32 when n >= 256) and rot_apply_f32 (k <= 48)
+take when A is TMA-addressable: bit-exact against the
 oracles on ragged shapes, padded leading dimensions, every k from 1 to 8 (so
 every window size and the k < window case), several passes (k = 9, 16, 23,
 48), and the full 8192 x 8192 matrix at k = 1.  Leading dimensions the stream
