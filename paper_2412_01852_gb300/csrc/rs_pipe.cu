@@ -180,12 +180,49 @@ __device__ __forceinline__ void write_group(T* buf, int q, int g, const T (&v)[R
   }
 }
 
+// 16 bytes into shared memory, stored only where `on` holds: a predicated
+// store, so the warp takes no branch around the group's last lane.
+__device__ __forceinline__ void st_shared_if(float* p, const Chunk<float>& x, bool on) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n @q st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n}\n"
+               ::"r"(smem_u32(p)), "f"(x.e[0]), "f"(x.e[1]), "f"(x.e[2]), "f"(x.e[3]), "r"((int)on) : "memory");
+}
+__device__ __forceinline__ void st_shared_if(double* p, const Chunk<double>& x, bool on) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %3, 0;\n @q st.shared.v2.f64 [%0], {%1, %2};\n}\n"
+               ::"r"(smem_u32(p)), "d"(x.e[0]), "d"(x.e[1]), "r"((int)on) : "memory");
+}
+
+// write_group by the lanes where `on` holds (every lane computes the slots).
+template <typename T, int SPL, int G, int R>
+__device__ __forceinline__ void write_group_if(T* buf, int q, int g, const T (&v)[R], bool on) {
+  using PC = Pipe<T, SPL, G, R>;
+#pragma unroll
+  for (int c = 0; c < PC::CPG; ++c) {
+    Chunk<T> x;
+#pragma unroll
+    for (int e = 0; e < PC::EPC; ++e) {
+      const int i = c * PC::EPC + e;
+      x.e[e] = i < R ? v[i < R ? i : 0] : T(0);
+    }
+    st_shared_if(buf + chunk_at<PC::NCH>(q, g * PC::CPG + c) * PC::EPC, x, on);
+  }
+}
+
+template <typename T>
+constexpr bool kLateSelect = sizeof(T) == 4;
+
 // One step t = t0 + u.  cs / in: this step's pairs and stage-0 input;
 // ncs / nin receive the next step's (the pairs from shared memory, the
 // input as the shuffle of this step's last-stage output, for a group's
 // first lane column nq of nin_buf).  The lane's last stage runs first, so
 // the shuffles overlap the other stages.  FAST: every stage of every lane
 // has its rotation.
+//
+// FP32 (kLateSelect): the group's last lane stores its output with a
+// predicated store instead of a branch, and the first lane's choice of its
+// next input comes last, after the shuffle and shared-memory results have
+// arrived (with four steps per iteration, 2.93 -> 2.73 ms at 8192 x 8192,
+// k = 192).  FP64 keeps the branch and the early choice: the late form
+// made k = 16 slower by 1.5 %.
 template <typename T, int SPL, int G, int R, bool FAST>
 __device__ __forceinline__ void pipe_step(PipeState<T, SPL, R>& st, const typename Pair<T>::type (&cs)[SPL],
                                           const T (&in)[R], typename Pair<T>::type (&ncs)[SPL], T (&nin)[R],
@@ -210,9 +247,11 @@ __device__ __forceinline__ void pipe_step(PipeState<T, SPL, R>& st, const typena
     pipe_stage<T, R, FAST>(st.carry[0], in, st.last, cs[0].x, cs[0].y, on[0]);
 #pragma unroll
   for (int i = 0; i < R; ++i) nin[i] = __shfl_up_sync(0xffffffffu, st.last[i], 1, PC::LPG);
-  if (pl == 0) {
+  if constexpr (!kLateSelect<T>) {
+    if (pl == 0) {
 #pragma unroll
-    for (int i = 0; i < R; ++i) nin[i] = nv[i];
+      for (int i = 0; i < R; ++i) nin[i] = nv[i];
+    }
   }
   // Then stage SPL-2 down to 0: stage s reads stage s-1's output of the
   // previous step before stage s-1 replaces it.
@@ -220,11 +259,18 @@ __device__ __forceinline__ void pipe_step(PipeState<T, SPL, R>& st, const typena
   for (int s = SPL - 2; s >= 1; --s)
     pipe_stage<T, R, FAST>(st.carry[s], st.prev[s - 1], st.prev[s], cs[s].x, cs[s].y, on[s]);
   if constexpr (SPL > 1) pipe_stage<T, R, FAST>(st.carry[0], in, st.prev[0], cs[0].x, cs[0].y, on[0]);
-  if (pl == PC::LPG - 1) write_group<T, SPL, G, R>(outb, u, g, st.last);
+  if constexpr (kLateSelect<T>) {
+    write_group_if<T, SPL, G, R>(outb, u, g, st.last, pl == PC::LPG - 1);
+#pragma unroll
+    for (int i = 0; i < R; ++i) nin[i] = pl == 0 ? nv[i] : nin[i];
+  } else {
+    if (pl == PC::LPG - 1) write_group<T, SPL, G, R>(outb, u, g, st.last);
+  }
 }
 
-// 32 steps t0 .. t0+31, two per iteration with the current and next
-// registers trading places (no copies).  cst: this lane's pairs of the
+// 32 steps t0 .. t0+31, the current and next registers trading places
+// every step (no copies): four steps per iteration in FP32, two in FP64 (at
+// 8192 x 8192, four made FP32 6 % faster and FP64 at k = 8 3 % slower).  cst: this lane's pairs of the
 // tile's first step (shared memory); inb / inb_next: this tile's and the
 // next tile's input columns; in: stage 0's input of step t0, on return that
 // of step t0 + 32.
@@ -237,13 +283,28 @@ __device__ __forceinline__ void pipe_tile(PipeState<T, SPL, R>& st, T (&in)[R], 
   typename PC::P2 csA[SPL], csB[SPL];
   T inB[R];
   load_pairs<typename PC::P2, SPL>(cst, csA);
+  if constexpr (sizeof(T) == 4) {
 #pragma unroll 1
-  for (int u = 0; u < kPTC; u += 2) {
-    pipe_step<T, SPL, G, R, FAST>(st, csA, in, csB, inB, true, cst + (u + 1) * KS, inb, u + 1, outb, u, t0 + u, n,
-                                  kp, g, pl);
-    const bool end = u + 2 >= kPTC;
-    pipe_step<T, SPL, G, R, FAST>(st, csB, inB, csA, in, !end, cst + (u + 2) * KS, end ? inb_next : inb,
-                                  (u + 2) & (kPTC - 1), outb, u + 1, t0 + u + 1, n, kp, g, pl);
+    for (int u = 0; u < kPTC; u += 4) {
+      pipe_step<T, SPL, G, R, FAST>(st, csA, in, csB, inB, true, cst + (u + 1) * KS, inb, u + 1, outb, u, t0 + u, n,
+                                    kp, g, pl);
+      pipe_step<T, SPL, G, R, FAST>(st, csB, inB, csA, in, true, cst + (u + 2) * KS, inb, u + 2, outb, u + 1,
+                                    t0 + u + 1, n, kp, g, pl);
+      pipe_step<T, SPL, G, R, FAST>(st, csA, in, csB, inB, true, cst + (u + 3) * KS, inb, u + 3, outb, u + 2,
+                                    t0 + u + 2, n, kp, g, pl);
+      const bool end = u + 4 >= kPTC;
+      pipe_step<T, SPL, G, R, FAST>(st, csB, inB, csA, in, !end, cst + (u + 4) * KS, end ? inb_next : inb,
+                                    (u + 4) & (kPTC - 1), outb, u + 3, t0 + u + 3, n, kp, g, pl);
+    }
+  } else {
+#pragma unroll 1
+    for (int u = 0; u < kPTC; u += 2) {
+      pipe_step<T, SPL, G, R, FAST>(st, csA, in, csB, inB, true, cst + (u + 1) * KS, inb, u + 1, outb, u, t0 + u, n,
+                                    kp, g, pl);
+      const bool end = u + 2 >= kPTC;
+      pipe_step<T, SPL, G, R, FAST>(st, csB, inB, csA, in, !end, cst + (u + 2) * KS, end ? inb_next : inb,
+                                    (u + 2) & (kPTC - 1), outb, u + 1, t0 + u + 1, n, kp, g, pl);
+    }
   }
 }
 
