@@ -270,10 +270,10 @@ __device__ __forceinline__ void pipe_step(PipeState<T, SPL, R>& st, const typena
 
 // 32 steps t0 .. t0+31, the current and next registers trading places
 // every step (no copies): four steps per iteration in FP32, two in FP64 (at
-// 8192 x 8192, four made FP32 6 % faster and FP64 at k = 8 3 % slower).  cst: this lane's pairs of the
-// tile's first step (shared memory); inb / inb_next: this tile's and the
-// next tile's input columns; in: stage 0's input of step t0, on return that
-// of step t0 + 32.
+// 8192 x 8192, four made FP32 6 % faster and FP64 at k = 8 3 % slower).
+// cst: this lane's pairs of the tile's first step (shared memory); inb /
+// inb_next: this tile's and the next tile's input columns; in: stage 0's
+// input of step t0, on return that of step t0 + 32.
 template <typename T, int SPL, int G, int R, bool FAST>
 __device__ __forceinline__ void pipe_tile(PipeState<T, SPL, R>& st, T (&in)[R], const T* inb, const T* inb_next,
                                           T* outb, const typename Pair<T>::type* cst, int t0, int n, int kp, int g,
