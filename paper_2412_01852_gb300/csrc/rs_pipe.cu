@@ -21,10 +21,11 @@
 // stream a stage without a rotation passes its values through unchanged, so
 // zeros keep their sign and infinities stay.
 //
-// FP32 (k >= 32): one group, up to 192 stages per pass, 7 rows.  FP64
-// (3 <= k <= 32): GB300's FP64 unit takes as long for a warp instruction
-// whatever its active lanes, so every lane holds a stage: k is rounded up to
-// a power of two KS and the warp holds 32/KS independent groups.
+// FP32 (k >= 32): one group, up to 192 stages per pass, 7 rows, 4 warps per
+// CTA.  FP64 (3 <= k <= 32): GB300's FP64 unit takes as long for a warp
+// instruction whatever its active lanes, so every lane holds a stage: k is
+// rounded up to a power of two KS and the warp holds 32/KS independent
+// groups; CTAs of one warp up to KS = 16, of 4 warps at KS = 32.
 //
 // The warps of a CTA run in step and share the (c,s) table through shared
 // memory: one bulk copy per 32-step tile, two or three tiles in flight,
@@ -40,10 +41,10 @@ namespace rs {
 namespace {
 
 constexpr int kPTC = 32;      // steps (columns) per tile
-constexpr int kPWarps = 4;    // warps per CTA
 constexpr int kPMaxSpl = 6;   // FP32 sequences per lane: 192 per pass
 
-template <typename T, int SPL, int G, int R>
+// W: warps per CTA.
+template <typename T, int SPL, int G, int R, int W = 4>
 struct Pipe {
   using P2 = typename Pair<T>::type;
   static constexpr int LPG = 32 / G;                             // lanes per group
@@ -56,7 +57,7 @@ struct Pipe {
   static constexpr int kTabBytes = kPTC * KS * (int)sizeof(P2);  // (c,s) of one 32-step tile
   static constexpr int NS = kTabBytes >= 32768 ? 2 : 3;          // table tiles in flight
   static constexpr int kWarpElems = 3 * kPTC * SLOT;             // two input tiles, one output tile
-  static constexpr int kSmem = NS * kTabBytes + kPWarps * kWarpElems * (int)sizeof(T) + NS * 8;
+  static constexpr int kSmem = NS * kTabBytes + W * kWarpElems * (int)sizeof(T) + NS * 8;
   static_assert(NCH == 1 || NCH == 2 || NCH == 4 || NCH == 8, "column slot of 1, 2, 4 or 8 chunks");
   static_assert(32 % G == 0, "groups split the warp evenly");
 };
@@ -308,21 +309,21 @@ __device__ __forceinline__ void pipe_tile(PipeState<T, SPL, R>& st, T (&in)[R], 
   }
 }
 
-// One CTA: kPWarps warps of G*R rows each, in step with each other; the
-// (c,s) table flows through NS shared tiles (one bulk copy per 32 steps,
-// bounded waits).
-template <typename T, int SPL, int G, int R>
-__global__ void __launch_bounds__(kPWarps * 32)
+// One CTA: W warps of G*R rows each, in step with each other; the (c,s)
+// table flows through NS shared tiles (one bulk copy per 32 steps, bounded
+// waits).
+template <typename T, int SPL, int G, int R, int W>
+__global__ void __launch_bounds__(W * 32)
 pipe_kernel(const typename Pair<T>::type* __restrict__ tab, int NT, T* __restrict__ A, int64_t lda, int m, int n,
             int kp, int* status) {
-  using PC = Pipe<T, SPL, G, R>;
+  using PC = Pipe<T, SPL, G, R, W>;
   using P2 = typename PC::P2;
   constexpr int KS = PC::KS, NS = PC::NS, ROWS = PC::ROWS, SLOT = PC::SLOT;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NS * PC::kTabBytes + kPWarps * PC::kWarpElems * sizeof(T));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NS * PC::kTabBytes + W * PC::kWarpElems * sizeof(T));
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int g = lane / PC::LPG, pl = lane % PC::LPG;
-  const int r0 = (blockIdx.x * kPWarps + wid) * ROWS;
+  const int r0 = (blockIdx.x * W + wid) * ROWS;
   const bool active = r0 < m;                   // idle warps still take part in the barriers
   const int nrow = active ? min(ROWS, m - r0) : 0;
   T* wb = reinterpret_cast<T*>(smem + NS * PC::kTabBytes) + wid * PC::kWarpElems;
@@ -425,15 +426,15 @@ pipe_kernel(const typename Pair<T>::type* __restrict__ tab, int NT, T* __restric
     for (int r = Ti; r < ntiles && r < Ti + NS; ++r) (void)mbar_wait_bounded(&bar[r % NS], (uint32_t)(r / NS) & 1u);
 }
 
-template <typename T, int SPL, int G, int R>
+template <typename T, int SPL, int G, int R, int W = 4>
 cudaError_t launch_pipe(const typename Pair<T>::type* tab, int NT, T* A, int64_t lda, int m, int n, int kp,
                         int* status, cudaStream_t s) {
-  using PC = Pipe<T, SPL, G, R>;
-  const int rows = kPWarps * PC::ROWS;
-  auto kfn = pipe_kernel<T, SPL, G, R>;
+  using PC = Pipe<T, SPL, G, R, W>;
+  const int rows = W * PC::ROWS;
+  auto kfn = pipe_kernel<T, SPL, G, R, W>;
   cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(kfn), PC::kSmem);
   if (e != cudaSuccess) return e;
-  kfn<<<(unsigned)((m + rows - 1) / rows), kPWarps * 32, PC::kSmem, s>>>(tab, NT, A, lda, m, n, kp, status);
+  kfn<<<(unsigned)((m + rows - 1) / rows), W * 32, PC::kSmem, s>>>(tab, NT, A, lda, m, n, kp, status);
   return cudaGetLastError();
 }
 
@@ -548,7 +549,12 @@ rot_status pipe_apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t ld
                           const double* S, int64_t lds, cudaStream_t s) {
   // One pass; every lane holds one stage: KS = k rounded up to a power of
   // two lanes per group (stages past k pass their values through), 32/KS
-  // groups per warp, about 8 rows per warp.
+  // groups per warp, about 8 rows per warp.  Up to 16 stages a CTA is one
+  // warp: 8192 rows then make 1024 CTAs, at most 7 (56 rows) per SM where
+  // 4-warp CTAs put 64 rows on some SMs and 32 on others, and the SM's
+  // FP64 unit takes time in proportion to its rows (k = 8: 4.86 -> 4.09 ms,
+  // k = 16: 9.33 -> 8.04 ms at 8192 x 8192).  At 32 stages the table tiles
+  // leave room for only 4 one-warp CTAs per SM (18.4 ms against 16.3).
   int KS = 4;
   while (KS < k) KS *= 2;
   PipeScratch<double> ps;
@@ -560,10 +566,10 @@ rot_status pipe_apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t ld
     const int tr = trace_begin(ROT_KERNEL_PIPE_F64, m * (n - 1) * k, s);
     cudaError_t e;
     switch (KS) {
-      case 4: e = launch_pipe<double, 1, 8, 1>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
-      case 8: e = launch_pipe<double, 1, 4, 2>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
-      case 16: e = launch_pipe<double, 1, 2, 4>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
-      default: e = launch_pipe<double, 1, 1, 7>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
+      case 4: e = launch_pipe<double, 1, 8, 1, 1>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
+      case 8: e = launch_pipe<double, 1, 4, 2, 1>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
+      case 16: e = launch_pipe<double, 1, 2, 4, 1>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
+      default: e = launch_pipe<double, 1, 1, 7, 4>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
     }
     trace_end(tr, s);
     if (e != cudaSuccess) st = cuda_failed(e, "pipe_f64: kernel launch");
