@@ -545,39 +545,65 @@ bool pipe_f64_fits(int64_t m, int64_t n, int64_t k) {
   return k >= 3 && k <= 32 && n >= 256 && m >= 1 && m < (int64_t(1) << 31) && n < (int64_t(1) << 30);
 }
 
+int pipe_f64_passes(int64_t k, bool tail_on_stream, int (&KS)[4], int (&kp)[4]) {
+  // Every lane holds one stage, so a pass costs its KS (k rounded up to a
+  // power of two) whatever the sequences it applies.  So k runs as passes of
+  // powers of two from 32 down to 4 (the binary digits of k rounded up to a
+  // multiple of 4), the last one short by that rounding; a single sequence
+  // left over (k = 4j + 1) goes to the column stream when it applies.
+  const int64_t kt = tail_on_stream ? k - 1 : k;
+  const int64_t q = (kt + 3) / 4 * 4;
+  int np = 0;
+  for (int b = 32; b >= 4; b /= 2)
+    if (q & b) {
+      KS[np] = b;
+      kp[np] = b;
+      ++np;
+    }
+  kp[np - 1] -= (int)(q - kt);
+  return np;
+}
+
 rot_status pipe_apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C, int64_t ldc,
                           const double* S, int64_t lds, cudaStream_t s) {
-  // One pass; every lane holds one stage: KS = k rounded up to a power of
-  // two lanes per group (stages past k pass their values through), 32/KS
-  // groups per warp, about 8 rows per warp.  Up to 16 stages a CTA is one
-  // warp: 8192 rows then make 1024 CTAs, at most 7 (56 rows) per SM where
-  // 4-warp CTAs put 64 rows on some SMs and 32 on others, and the SM's
-  // FP64 unit takes time in proportion to its rows (k = 8: 4.86 -> 4.09 ms,
-  // k = 16: 9.33 -> 8.04 ms at 8192 x 8192).  At 32 stages the table tiles
-  // leave room for only 4 one-warp CTAs per SM (18.4 ms against 16.3).
-  int KS = 4;
-  while (KS < k) KS *= 2;
+  // Passes (pipe_f64_passes), each applying its sequences entirely before
+  // the next, as Algorithm 2 does.  Every lane holds one stage of a group
+  // of KS lanes (stages past a pass's sequences pass their values through),
+  // 32/KS groups per warp, about 8 rows per warp.  Up to 16 stages a CTA is
+  // one warp: 8192 rows then make 1024 CTAs, at most 7 (56 rows) per SM
+  // where 4-warp CTAs put 64 rows on some SMs and 32 on others, and the
+  // SM's FP64 unit takes time in proportion to its rows (k = 8: 4.86 ->
+  // 4.09 ms, k = 16: 9.33 -> 8.04 ms at 8192 x 8192).  At 32 stages the
+  // table tiles leave room for only 4 one-warp CTAs per SM (18.4 ms against
+  // 16.3).
+  const bool tail = k % 4 == 1 && stream_fits<double>(m, n, 1, A, lda);
+  int KS[4], kp[4];
+  const int np = pipe_f64_passes(k, tail, KS, kp);
   PipeScratch<double> ps;
-  rot_status st = pipe_scratch<double>(n, KS, s, &ps);
+  rot_status st = pipe_scratch<double>(n, KS[0], s, &ps);
   if (st != ROT_OK) return st;
-  int NT = 0;
-  st = pipe_table<double>(n, (int)k, KS, C, ldc, S, lds, ps, s, &NT);
-  if (st == ROT_OK) {
-    const int tr = trace_begin(ROT_KERNEL_PIPE_F64, m * (n - 1) * k, s);
+  int64_t p0 = 0;
+  for (int i = 0; i < np && st == ROT_OK; ++i) {
+    int NT = 0;
+    st = pipe_table<double>(n, kp[i], KS[i], C + p0 * ldc, ldc, S + p0 * lds, lds, ps, s, &NT);
+    if (st != ROT_OK) break;
+    const int tr = trace_begin(ROT_KERNEL_PIPE_F64, m * (n - 1) * kp[i], s);
     cudaError_t e;
-    switch (KS) {
-      case 4: e = launch_pipe<double, 1, 8, 1, 1>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
-      case 8: e = launch_pipe<double, 1, 4, 2, 1>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
-      case 16: e = launch_pipe<double, 1, 2, 4, 1>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
-      default: e = launch_pipe<double, 1, 1, 7, 4>(ps.tab, NT, A, lda, (int)m, (int)n, (int)k, ps.status, s); break;
+    switch (KS[i]) {
+      case 4: e = launch_pipe<double, 1, 8, 1, 1>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
+      case 8: e = launch_pipe<double, 1, 4, 2, 1>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
+      case 16: e = launch_pipe<double, 1, 2, 4, 1>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
+      default: e = launch_pipe<double, 1, 1, 7, 4>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
     }
     trace_end(tr, s);
-    if (e != cudaSuccess) st = cuda_failed(e, "pipe_f64: kernel launch");
-    else count_launches(2);
+    if (e != cudaSuccess) { st = cuda_failed(e, "pipe_f64: kernel launch"); break; }
+    count_launches(2);
+    p0 += kp[i];
   }
   if (st == ROT_OK) record_status_async(ps.status, s);
   cudaFreeAsync(ps.base, s);
-  return st;
+  if (st != ROT_OK || !tail) return st;
+  return stream_apply<double>(m, n, 1, A, lda, C + p0 * ldc, ldc, S + p0 * lds, lds, s);
 }
 
 }  // namespace rs

@@ -68,6 +68,10 @@ def test_pipe_f32_bit_exact(rs, m, n, k, slack):
 CASES64 = [  # m, n, k, lda slack: FP64, 3 <= k <= 32, n >= 256 (groups of 4, 8, 16 or 32 lanes)
     (8, 256, 3, 0), (9, 300, 4, 1), (33, 700, 5, 0), (100, 1024, 8, 3), (17, 257, 9, 0), (64, 1000, 16, 2),
     (5, 400, 17, 0), (71, 600, 31, 0), (40, 1100, 32, 1), (1, 256, 8, 0), (200, 333, 12, 0),
+    # k = 4j + 1 with m >= 64 and an even lda: passes, then the last sequence on the column stream
+    (64, 300, 5, 0), (100, 512, 13, 2), (128, 777, 21, 0), (96, 260, 29, 0),
+    # the same k with an odd lda (no column stream): the last pass takes it
+    (65, 300, 9, 0),
 ]
 
 
