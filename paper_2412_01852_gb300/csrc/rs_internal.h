@@ -60,9 +60,6 @@ bool pipe_f64_fits(int64_t m, int64_t n, int64_t k);
 // fewer sequences, the wavefront kernel otherwise.
 rot_status apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C, int64_t ldc,
                      const double* S, int64_t lds, cudaStream_t stream);
-// FP64 passes for k sequences: stages per group and sequences of each pass
-// (at most 4); with tail_on_stream the last sequence is left to the caller.
-int pipe_f64_passes(int64_t k, bool tail_on_stream, int (&KS)[4], int (&kp)[4]);
 rot_status pipe_apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C, int64_t ldc,
                           const double* S, int64_t lds, cudaStream_t stream);
 

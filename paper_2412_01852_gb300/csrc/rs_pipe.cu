@@ -545,7 +545,9 @@ bool pipe_f64_fits(int64_t m, int64_t n, int64_t k) {
   return k >= 3 && k <= 32 && n >= 256 && m >= 1 && m < (int64_t(1) << 31) && n < (int64_t(1) << 30);
 }
 
-int pipe_f64_passes(int64_t k, bool tail_on_stream, int (&KS)[4], int (&kp)[4]) {
+// FP64 passes for k sequences: stages per group and sequences of each pass
+// (at most 3); with tail_on_stream the last sequence is left to the caller.
+static int pipe_f64_passes(int64_t k, bool tail_on_stream, int (&KS)[4], int (&kp)[4]) {
   // Every lane holds one stage, so a pass costs its KS (k rounded up to a
   // power of two) whatever the sequences it applies.  So k runs as passes of
   // powers of two from 32 down to 4 (the binary digits of k rounded up to a
