@@ -23,6 +23,11 @@ Functions and the passages they follow:
 * ``rot_sequence_left``       -- the rotations applied to rows (Algorithm 2 on A^T).
 * ``refl_sequence_reverse``   -- the same reflectors in reverse order (their inverse).
 
+Beside the oracle, ``rot_sequence_parallel`` runs the multi-core CPU baseline
+(``rot_cpu_parallel.c``: row blocks over host threads as in Section 7, wave
+order inside each block).  It is the timed CPU leg of ``bench.py``, not a
+reference for anything; the tests check it bit for bit against the oracle.
+
 Parity status: every function is pinned by ``tests/test_oracle_pins.py`` (closed
 forms, exact special cases, invariants, BLAS ``drot`` and exact rational
 arithmetic); none is "parity unpinned".
@@ -40,6 +45,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rot_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "librot_oracle.so")
+_PAR_SRC = os.path.join(_HERE, "rot_cpu_parallel.c")
+_PAR_SO = os.path.join(_BUILD, "librot_cpu_parallel.so")
+_par_lib = None
+_par_openmp = None
 _lock = threading.Lock()
 _lib = None
 
@@ -57,7 +66,29 @@ def build(force: bool = False) -> str:
                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _SO)
+    build_parallel(force)
     return _SO
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile rot_cpu_parallel.c with OpenMP (or, if the compiler lacks it, without)."""
+    global _par_openmp
+    os.makedirs(_BUILD, exist_ok=True)
+    flag = _PAR_SO + ".openmp"
+    if force or not os.path.exists(_PAR_SO) or os.path.getmtime(_PAR_SO) < os.path.getmtime(_PAR_SRC):
+        tmp = _PAR_SO + ".%d.tmp" % os.getpid()
+        base = ["gcc", "-O3", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                "-o", tmp, _PAR_SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True)
+        openmp = r.returncode == 0
+        if not openmp:
+            subprocess.run(base, check=True)
+        os.replace(tmp, _PAR_SO)
+        with open(flag, "w") as f:
+            f.write("1" if openmp else "0")
+    with open(flag) as f:
+        _par_openmp = f.read().strip() == "1"
+    return _PAR_SO
 
 
 def _declare(lib):
@@ -282,3 +313,42 @@ def rot_sequence_gemm(A, C, S, nb, kb):
         Qs = Q[lo - c0:hi - c0, lo - c0:hi - c0]
         A[:, lo:hi] = A[:, lo:hi] @ Qs
     return A
+
+
+def _load_parallel():
+    global _par_lib
+    with _lock:
+        if _par_lib is None:
+            build()
+            lib = ctypes.CDLL(_PAR_SO)
+            lib.cpu_rot_sequence_parallel.argtypes = [_i64, _i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64,
+                                                      _i64, _i64, ctypes.c_int]
+            lib.cpu_rot_sequence_parallel.restype = ctypes.c_int
+            _par_lib = lib
+    return _par_lib
+
+
+def rot_sequence_parallel(A, C, S, mb=32, kb=32, threads=0, inplace=False):
+    """Multi-core CPU baseline: Algorithm 2's result from row blocks of mb rows on
+    `threads` host threads (0: all), kb sequences per pass in wave order.
+    Returns (A', threads used).  With inplace=True a Fortran-ordered float64 A
+    is updated in place (for timing without a copy)."""
+    lib = _load_parallel()
+    if not (inplace and isinstance(A, np.ndarray) and A.dtype == np.float64 and A.flags.f_contiguous):
+        A = _fortran(A, np.float64)
+    C = _fortran(C, np.float64)
+    S = _fortran(S, np.float64)
+    m, n, k = _check(A, C, S)
+    if m == 0 or n < 2 or k == 0:
+        return A, 1
+    used = lib.cpu_rot_sequence_parallel(m, n, k, _ptr(A, ctypes.c_double), max(1, m),
+                                         _ptr(C, ctypes.c_double), max(1, n - 1),
+                                         _ptr(S, ctypes.c_double), max(1, n - 1),
+                                         int(mb), int(kb), int(threads))
+    return A, int(used)
+
+
+def parallel_uses_openmp():
+    """Whether the CPU baseline was compiled with OpenMP."""
+    _load_parallel()
+    return bool(_par_openmp)
