@@ -181,23 +181,82 @@ def job_throughput(world_size, steps, units_per_step, seconds):
     return world_size * steps * units_per_step / seconds
 
 
-def cpu_baseline_leg(cfg, seconds):
-    """The oracle as it stands (one thread) on row blocks of the same instance."""
+def host_cores():
+    """Host CPU cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rows_threaded(A, C, S, row_blocks, threads, deadline=None):
+    """The oracle as it stands, run on row blocks by `threads` host threads at
+    once (rows are independent, and the C oracle releases the interpreter
+    while it runs).  Returns the number of rows done before the deadline."""
+    import threading
     import oracle
+    lock = threading.Lock()
+    todo = list(row_blocks)
+    done = [0]
+
+    def worker():
+        while True:
+            with lock:
+                if not todo or (deadline is not None and time.perf_counter() > deadline):
+                    return
+                r0, r1 = todo.pop(0)
+            oracle.rot_sequence(A[r0:r1], C, S)
+            with lock:
+                done[0] += r1 - r0
+
+    ts = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return done[0]
+
+
+def cpu_baseline_leg(cfg, seconds):
+    """The oracle as it stands, on row blocks of the same instance, on all host cores."""
+    import oracle
+    oracle.build()
     m, n, k, seed = cfg["m"], cfg["n"], cfg["k"], cfg["seed"]
     A = wl.matrix(m, n, seed)
     C, S = wl.rotations(n, k, seed)
-    block = ORACLE_BLOCK
-    rows = 0
+    cores = host_cores()
+    blocks = [(r, min(r + ORACLE_BLOCK, m)) for r in range(0, m, ORACLE_BLOCK)]
+    t0 = time.perf_counter()
+    rows = oracle_rows_threaded(A, C, S, blocks, cores, deadline=t0 + seconds)
+    el = time.perf_counter() - t0
+    return {"value": rows * (n - 1) * k / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of the %d rows of the %dx%d, k=%d instance (%d x %d x %d rotation-rows), in "
+                      "blocks of %d rows taken by %d host threads at once; plain Algorithm 2 in C, %.1f s"
+                      % (rows, m, m, n, k, rows, n - 1, k, ORACLE_BLOCK, cores, el)}
+
+
+def cpu_parallel_leg(cfg, seconds):
+    """The multi-core CPU baseline (row blocks over OpenMP threads, wave order
+    inside a block), bit-exact with the oracle, on the same instance."""
+    import oracle
+    oracle.build()
+    m, n, k, seed = cfg["m"], cfg["n"], cfg["k"], cfg["seed"]
+    A = np.asfortranarray(wl.matrix(m, n, seed))
+    C, S = wl.rotations(n, k, seed)
+    chunk = 1024
+    rows, used = 0, 1
     t0 = time.perf_counter()
     while rows < m and time.perf_counter() - t0 < seconds:
-        oracle.rot_sequence(A[rows:rows + block], C, S)
-        rows += block
+        r1 = min(rows + chunk, m)
+        blk = np.asfortranarray(A[rows:r1])
+        _, used = oracle.rot_sequence_parallel(blk, C, S, mb=32, kb=32, inplace=True)
+        rows = r1
     el = time.perf_counter() - t0
-    return {"value": rows * (n - 1) * k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "rows 0..%d of the %dx%d, k=%d instance (%d x %d x %d rotation-rows), "
-                      "in blocks of %d rows, plain Algorithm 2 in C, one thread, %.1f s"
-                      % (rows - 1, m, n, k, rows, n - 1, k, ORACLE_BLOCK, el)}
+    return {"value": rows * (n - 1) * k / el, "unit": UNIT, "cores": used,
+            "kind": "openmp row blocks, wave order (bit-exact with the oracle)",
+            "openmp": oracle.parallel_uses_openmp(),
+            "sample": "%d of the %d rows of the %dx%d, k=%d instance in chunks of %d rows; 32-row blocks "
+                      "over %d threads, 32 sequences per pass, %.1f s" % (rows, m, m, n, k, chunk, used, el)}
 
 
 def run_reference(args, cfg):
@@ -205,14 +264,17 @@ def run_reference(args, cfg):
     if rank != 0:
         return
     import oracle
+    oracle.build()
     m, n, k, seed = cfg["m"], cfg["n"], cfg["k"], cfg["seed"]
     A = wl.matrix(m, n, seed)
     C, S = wl.rotations(n, k, seed)
-    rows = args.ref_rows
+    rows = min(args.ref_rows, m) if args.ref_rows > 0 else m
+    cores = host_cores()
 
     def one_step(r0):
-        for b in range(r0, r0 + rows, ORACLE_BLOCK):
-            oracle.rot_sequence(A[b:min(b + ORACLE_BLOCK, r0 + rows)], C, S)
+        blocks = [(b, min(b + ORACLE_BLOCK, r0 + rows)) for b in range(r0, r0 + rows, ORACLE_BLOCK)]
+        done = oracle_rows_threaded(A, C, S, blocks, cores)
+        assert done == rows
 
     for i in range(args.warmup):
         one_step(0)
@@ -230,9 +292,10 @@ def run_reference(args, cfg):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_block(cfg, ws),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d rows per step of the %dx%d, k=%d instance, in blocks of %d "
-                                   "rows; plain Algorithm 2 in C, one thread" % (rows, m, n, k, ORACLE_BLOCK)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d rows per step of the %dx%d, k=%d instance, in blocks of %d rows taken "
+                                   "by %d host threads at once; plain Algorithm 2 in C"
+                                   % (rows, m, n, k, ORACLE_BLOCK, cores)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -255,13 +318,20 @@ def main():
     ap.add_argument("--workload", default="plain-8192")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--ref-rows", type=int, default=512)
+    ap.add_argument("--ref-rows", type=int, default=0,
+                    help="rows of the instance per reference step (0: all of them)")
     ap.add_argument("--variant", default="plain",
                     choices=["plain", "f32", "gemm-f16", "gemm-bf16", "gemm-dmma", "gemm-f16-q32",
                              "gemm-bf16-q32", "batched", "serving", "reflectors", "left", "small-k"],
                     help="plain (default) is the measured line; the others measure the other "
                          "paths of the library on the same GPU")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--variants", default="f32,gemm-bf16,batched,serving",
+                    help="other paths measured after the plain line and reported in its 'variants' "
+                         "object ('none' to skip)")
+    ap.add_argument("--variant-steps", type=int, default=5)
+    ap.add_argument("--variant-serve-requests", type=int, default=2000,
+                    help="requests per offered-load level in the embedded serving measurement")
     ap.add_argument("--serve-batch", type=int, default=64, help="requests per launch in the serving variant")
     ap.add_argument("--serve-streams", type=int, default=8, help="server streams in the serving variant")
     ap.add_argument("--serve-fuse-k", type=int, default=192,
@@ -306,6 +376,14 @@ def main():
     stream = torch.cuda.current_stream()
 
     peak_gflops, _ = api.measure_fp64_peak()
+    # The rotation's own FP64 instruction mix (2 DMUL + 2 DFMA per rotation-row),
+    # registers only, at the wave kernel's launch shape (2 CTAs x 8 warps per SM)
+    # and at full occupancy: the best of these is the measured rotation ceiling.
+    mix = {}
+    for kind in ("rotation", "rotation_smem", "dfma", "dmul"):
+        for wpc, cps in ((8, 2), (32, 2)):
+            r, _ = api.measure_fp64_mix(kind, wpc, cps)
+            mix["%s_%dw" % (kind, wpc * cps)] = r
 
     for _ in range(args.warmup):
         rs.rot_apply(Ad, Cd, Sd)
@@ -339,6 +417,7 @@ def main():
     max_clk_ghz = nominal_sm_clock_ghz(dev)
     peak_tflops = props.multi_processor_count * FP64_FMA_PER_SM_CLK * 2 * max_clk_ghz / 1e3
     traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["kernel_src_sha"] == kernel_src_sha() else None
+    rot_probe_tflops = max(v for kname, v in mix.items() if kname.startswith("rotation")) * 6 / 4 / 1e12
 
     # ---- end to end through the host-buffer entry point ---------------------------
     Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True)
@@ -360,6 +439,25 @@ def main():
 
     cpu = (cpu_baseline_leg(cfg, args.cpu_seconds)
            if (rank == 0 and ws == 1 and args.cpu_seconds > 0) else None)
+    cpu_par = (cpu_parallel_leg(cfg, args.cpu_seconds)
+               if (rank == 0 and ws == 1 and args.cpu_seconds > 0) else None)
+
+    # ---- the other forms of the path on the same GPU (after the timed region) ------
+    variants = None
+    if rank == 0 and ws == 1 and args.variants not in ("", "none"):
+        variants = {}
+        for name in args.variants.split(","):
+            va = argparse.Namespace(**vars(args))
+            va.variant = name
+            va.steps = args.variant_steps
+            va.warmup = 3
+            va.serve_requests = args.variant_serve_requests
+            t_v = time.perf_counter()
+            v = variant_line(va)
+            for key in ("metric", "unit", "n_gpus", "higher_is_better", "data", "variant"):
+                v.pop(key, None)
+            v["wall_s"] = time.perf_counter() - t_v
+            variants[name] = v
 
     if rank == 0:
         line = {
@@ -376,12 +474,21 @@ def main():
                                                                    FP64_FMA_PER_SM_CLK, max_clk_ghz),
                          "dfma_probe_tflops": peak_gflops / 1e3,
                          "frac_of_dfma_probe": achieved_tflops / (peak_gflops / 1e3) if peak_gflops else None,
-                         "rotation_ceiling_frac": 0.75},
+                         "rotation_ceiling_frac": 0.75,
+                         "fp64_pipe_lanes_per_s_probes": mix,
+                         "rotation_probe_tflops": rot_probe_tflops,
+                         "frac_of_rotation_probe": achieved_tflops / rot_probe_tflops,
+                         "rotation_probe": "best FP64 rate of the rotation's own instruction mix (2 DMUL + 2 "
+                                           "DFMA per rotation-row), registers only, (c,s) in registers or read "
+                                           "from shared memory, 16 or 64 warps per SM; 6 flops per 4 lane-ops"},
             "cpu_baseline": cpu,
+            "cpu_parallel": cpu_par,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
+        if variants is not None:
+            line["variants"] = variants
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -444,6 +551,11 @@ def _measured_peaks():
 
 
 def run_variant(args):
+    print(json.dumps(variant_line(args)), flush=True)
+
+
+def variant_line(args):
+    """Measure one of the library's other paths; returns its JSON line (a dict)."""
     import torch
     import paper_2412_01852_gb300 as rs
     from paper_2412_01852_gb300 import api, build
@@ -501,9 +613,10 @@ def run_variant(args):
         ms = _timed_steps(torch, fn, args.steps, args.warmup, stream)
         recs = api.trace_stop()
         rs.rot_device_status()
-        by = {}
+        by, work_by = {}, {}
         for r in recs:
             by.setdefault(r[0], []).append(r[1])
+            work_by.setdefault(r[0], []).append(r[2])
         kernels = {kname: sum(v) / len(v) for kname, v in by.items()}
         steps_traced = max(len(v) for v in by.values())
         per_step = {kname: sum(v) / steps_traced for kname, v in by.items()}
@@ -524,21 +637,25 @@ def run_variant(args):
         else:
             kms = kernels.get("form_blocks", 0.0)
             nblk = api.form_blocks_count(n, k, cfg["nb"], cfg["kb"])
-            form_rows = nblk * (cfg["nb"] + cfg["kb"]) * cfg["nb"] * cfg["kb"]
+            # Rotation-row updates the formation kernel executed, as its launch
+            # reports them (waves where a block's rows are still zero are
+            # skipped in FP64; the FP32 pipeline also runs its (1,0) stages).
+            fw = work_by.get("form_blocks", [0])
+            form_rows = sum(fw) / len(fw)
             q32 = cfg_line["mode"].endswith("-q32")
             fpeak = fp32_peak if q32 else fp64_peak
             line["roofline"] = {"bound": "alu",
                                 "kernel": "form32_kernel (block formation, FP32 lane pipeline)" if q32 else
                                           "wave_batched_kernel (block formation, FP64)",
                                 "achieved": 6.0 * form_rows / (kms * 1e-3) / 1e12, "peak": fpeak,
-                                "unit": "TFLOP/s", "kernel_ms": kms,
+                                "unit": "TFLOP/s", "kernel_ms": kms, "executed_rotation_rows": form_rows,
+                                "share_of_step": kms / (ms / args.steps),
+                                "rotation_ceiling_frac": 0.75,
                                 "peak_source": "nominal %s FMA rate: SMs x %d x 2 x max SM clock"
                                                % (("FP32", FP32_FMA_PER_SM_CLK) if q32 else
                                                   ("FP64", FP64_FMA_PER_SM_CLK)),
-                                "note": "achieved counts the rotations of all blocks on full identity rows "
-                                        "(%s)" % ("the pipeline also runs (1,0) stages outside the block"
-                                                  if q32 else "zero waves are skipped, so this overstates "
-                                                              "executed flops")}
+                                "note": "achieved counts the rotation-row updates the kernel executed "
+                                        "(6 flops each), as its trace record reports them"}
             line["roofline"]["frac"] = line["roofline"]["achieved"] / fpeak
             # The block apply on its own: 2*L^2 flops per row and block per product.
             akms = kernels.get("gemm_apply", 0.0)
@@ -571,8 +688,7 @@ def run_variant(args):
                     ap.update({"mma_issue_ns": ns, "mmas_per_tile_block": per_block,
                                "issue_floor_ms": floor_ms, "frac_of_issue_floor": floor_ms / akms})
                 line["apply_roofline"] = ap
-        print(json.dumps(line), flush=True)
-        return
+        return line
 
     if args.variant == "reflectors":
         cfg = wl.WORKLOADS["plain-8192"]
@@ -595,8 +711,7 @@ def run_variant(args):
                                   "achieved": 6.0 * W / (kms * 1e-3) / 1e12, "peak": fp64_peak,
                                   "unit": "TFLOP/s"}})
         line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
-        print(json.dumps(line), flush=True)
-        return
+        return line
 
     if args.variant == "small-k":
         # Few sequences: one HBM pass over A carries little arithmetic, so FP32
@@ -683,8 +798,7 @@ def run_variant(args):
                                   "algorithmic_bytes": first["bytes"],
                                   "traffic": NCU_TRAFFIC_STREAM["bytes"]
                                   if NCU_TRAFFIC_STREAM["kernel_src_sha"] == stream_src_sha() else None}})
-        print(json.dumps(line), flush=True)
-        return
+        return line
 
     if args.variant == "left":
         # Rotations mixing the rows of A (C, S are (m-1) x k): A is transposed in
@@ -710,8 +824,7 @@ def run_variant(args):
                                   "kernel_ms": kms, "achieved": 6.0 * W / (kms * 1e-3) / 1e12,
                                   "peak": fp64_peak, "unit": "TFLOP/s"}})
         line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
-        print(json.dumps(line), flush=True)
-        return
+        return line
 
     if args.variant == "batched":
         shapes = wl.batch_shapes(512, seed=4)
@@ -753,8 +866,7 @@ def run_variant(args):
         line["roofline"]["achieved"] = 6.0 * W / (line["roofline"]["kernel_ms"] * 1e-3) / 1e12
         line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
         plan.close()
-        print(json.dumps(line), flush=True)
-        return
+        return line
 
     if args.variant == "serving":
         sizes = wl.SERVING_SIZES
@@ -786,6 +898,24 @@ def run_variant(args):
         el = time.perf_counter() - t0
         cap_rps = len(burst) / el
         st_burst = srv.stats(reset=True)
+        # each size class alone on the idle server: one request at a time
+        alone = {}
+        for nsz in sizes:
+            row = {}
+            for kk in (33, 64):
+                lat = []
+                for i in range(5):
+                    C, S = pool[nsz][i % 4]
+                    t = srv.submit(handles[nsz][i % per_size], C[:, :kk], S[:, :kk])
+                    lat.append(srv.wait_latency(t))
+                row["k%d_ms" % kk] = float(np.median(lat))
+            alone[str(nsz)] = row
+        srv.stats(reset=True)
+
+        def pct(xs, q):
+            xs = sorted(xs)
+            return xs[min(len(xs) - 1, max(0, int(np.ceil(q * len(xs))) - 1))] if xs else None
+
         levels = []
         for frac in (0.25, 0.5, 0.9):
             trace = wl.serving_trace(args.serve_requests, frac * cap_rps, seed=5 + int(frac * 100))
@@ -795,15 +925,19 @@ def run_variant(args):
                 d = t0 + r.arrival_s - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-                tk.append(submit(r)[0])
-            for t in tk:
-                srv.wait(t)
+                tk.append((submit(r)[0], r.n))
+            by_n = {}
+            for t, nsz in tk:
+                by_n.setdefault(nsz, []).append(srv.wait_latency(t))
             st = srv.stats(reset=True)
+            per_class = {str(nsz): {"requests": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99),
+                                    "max_ms": max(v)} for nsz, v in sorted(by_n.items())}
             levels.append({"offered_load": frac, "offered_rps": frac * cap_rps, "requests": len(trace),
                            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
                            "throughput_rot_rows_per_s": st["rotation_rows_per_s"],
                            "achieved_rps": st["completed"] / st["busy_s"] if st["busy_s"] > 0 else 0,
-                           "mean_batch": st["mean_batch"], "launches": st["launches"]})
+                           "mean_batch": st["mean_batch"], "launches": st["launches"],
+                           "per_size": per_class})
         srv.close()
         rs.rot_device_status()
         line.update({"value": st_burst["rotation_rows_per_s"], "dtype": "f64",
@@ -816,9 +950,9 @@ def run_variant(args):
                                            "max_fused_k": args.serve_fuse_k}},
                      "capacity": {"requests_per_s": cap_rps, "p50_ms": st_burst["p50_ms"],
                                   "p99_ms": st_burst["p99_ms"], "mean_batch": st_burst["mean_batch"]},
+                     "alone_latency_idle_gpu": alone,
                      "loads": levels})
-        print(json.dumps(line), flush=True)
-        return
+        return line
 
 
 if __name__ == "__main__":

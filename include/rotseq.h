@@ -147,19 +147,37 @@ rot_status rot_apply_host(int64_t m, int64_t n, int64_t k, double* A_host, int64
  *   counters (each part rounded up to 256 bytes, plus 256); a problem that
  *   needs more than 32 MiB is rejected with ROT_EINVAL and nothing is queued.
  *   (A 8192 x 8192, k = 192 problem needs 24.6 MiB.)
- *   Every GPU that loads the library keeps the 32 MiB array until the process
- *   exits.
- *   The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress, which can load the library's device code); make
- *   that first call before any stream capture.
+ *   The array exists on a device once the library's device code is loaded
+ *   there.  Under the CUDA runtime's lazy module loading (the default) that
+ *   happens at the first set-up on the device: rot_apply_noalloc_prepare()
+ *   or the first rot_apply_noalloc.  That set-up is the one moment the 32 MiB
+ *   come out of the device's free memory, so a caller that reserves the rest
+ *   of the GPU for its own pool makes it before reserving the pool, and
+ *   before any stream capture.  The array then stays until the process exits.
+ *   The set-up (cudaGetSymbolAddress for the array's device address, and the
+ *   kernel's shared-memory attribute) is done once per device and CUDA
+ *   context; after a device reset the next call repeats it.
  *   All calls share the one array; the counters are cleared at the start of
  *   each call, the rest is overwritten.  Calls whose work overlaps on the GPU
  *   (different streams, or host threads racing on one device) race on it and
  *   give wrong results: order them on one stream or synchronize in between.
+ *   Speed: this entry point always runs the wavefront kernel.  rot_apply
+ *   picks faster kernels for few sequences (k <= 32), whose scratch is
+ *   sized differently; at 8192 x 8192 with k = 8 this call takes about
+ *   twice as long as rot_apply.  For k > 32 the two run the same kernel.
+ *   rot_last_error() names the failing CUDA call on ROT_ECUDA.
  */
 rot_status rot_apply_noalloc(int64_t m, int64_t n, int64_t k, double* A, int64_t lda,
                              const double* C, int64_t ldc, const double* S, int64_t lds,
                              void* stream);
+
+/* The set-up of rot_apply_noalloc on the current device, without queuing any
+ * work: loads the library's device code there if needed (which creates the
+ * 32 MiB array), looks up the array's address and sets the kernel's
+ * shared-memory attribute.  Call it before reserving device memory for a pool
+ * and before stream capture; repeated calls are cheap.  ROT_ECUDA if a CUDA
+ * call fails (rot_last_error() names it).  The paper has no counterpart. */
+rot_status rot_apply_noalloc_prepare(void);
 
 /* ---- accumulated blocks applied by matrix products (rs_gemm, Section 8) -- */
 
@@ -405,6 +423,12 @@ rot_status rot_server_submit(rot_server* server, int handle, int64_t k, const do
  * has returned its status once. */
 rot_status rot_server_wait(rot_server* server, uint64_t ticket, int timeout_ms);
 
+/* rot_server_wait that also reports the request's latency: on ROT_OK (or a
+ * device-side ROT_ETIMEOUT) *latency_ms receives the time from its submission
+ * to the completion of its launch (the same clock as the statistics).  It is
+ * left alone when the wait itself runs out.  latency_ms may be NULL. */
+rot_status rot_server_wait_latency(rot_server* server, uint64_t ticket, int timeout_ms, double* latency_ms);
+
 /* Statistics since creation or the last reset (reset != 0 clears them). */
 rot_status rot_server_stats(rot_server* server, rot_server_stats_t* stats, int reset);
 
@@ -414,7 +438,11 @@ rot_status rot_server_destroy(rot_server* server);
 /* ---- measurement ------------------------------------------------------- */
 
 /* One traced kernel launch: its kind, device time and the rotation-row
- * updates (one rotation applied to one row) it performed. */
+ * updates (one rotation applied to one row) it performed.  For the block
+ * formation kernels (ROT_KERNEL_FORM_BLOCKS) `work` counts what the kernel
+ * executes: the FP64 formation skips the waves in which a chain's rows of
+ * the block are still zero, and the FP32 pipeline runs every stage of every
+ * step, (1,0) padding stages included. */
 typedef struct {
   int kind;      /* ROT_KERNEL_* */
   float ms;      /* CUDA-event time on the launch stream, -1 if unavailable */
@@ -449,6 +477,22 @@ int64_t rot_launch_count(void);
  * time of one probe launch.  Synchronous. */
 rot_status rot_measure_fp64_peak(double* gflops, double* ms);
 
+/* FP64 issue rate of one instruction mix, registers only, as a ceiling for
+ * the rotation kernels (the paper counts 6 flops per rotation-row; with the
+ * placement above that is 2 DMUL + 2 DFMA, Section 1.1):
+ *   kind 0  DFMA only      kind 1  DMUL only
+ *   kind 2  the rotation's mix: per pair sy = RN(s*y), sx = RN(s*x),
+ *           x' = fma(c,x,sy), y' = fma(c,y,-sx)
+ *   kind 3  kind 2 with (c, s) read from shared memory per rotation
+ * Every thread updates 4 independent pairs per iteration; the grid is
+ * ctas_per_sm CTAs of warps_per_cta warps per SM (warps_per_cta 1..32,
+ * ctas_per_sm 1..32, their product <= 64).  *lane_ops_per_s counts FP64
+ * instructions times the lanes that executed them, per second (a rotation
+ * applied to one row is 4 of them); *ms (optional) is one launch's time.
+ * ROT_EINVAL for out-of-range arguments.  Synchronous. */
+rot_status rot_measure_fp64_mix(int kind, int warps_per_cta, int ctas_per_sm, double* lane_ops_per_s,
+                                double* ms);
+
 /* Issue rate of the 5th-generation tensor cores for one product shape
  * (tcgen05.mma kind::f16, BF16 operands in shared memory, FP32 accumulator in
  * tensor memory, K = 16): one CTA per SM, one thread issues `mmas` products
@@ -476,10 +520,23 @@ rot_status rot_selftest_wait_timeout(int wait_ms, void* stream);
 
 /*
  * Synchronizes the current device, then returns and clears the sticky
- * device status: ROT_OK, or ROT_ETIMEOUT if a kernel's bounded wait ran out
- * since the last call, or ROT_ECUDA if the device reported an error.
+ * device status: ROT_OK; ROT_ETIMEOUT if a kernel's bounded wait ran out
+ * since the last call; ROT_ECUDA if the device reported an error (the
+ * synchronization failed, or a kernel recorded an internal error such as a
+ * work item decoded outside its problem).  rot_last_error() then names the
+ * cause.
  */
 rot_status rot_device_status(void);
+
+/*
+ * The rot_status a kernel's device status word stands for (host only, no
+ * CUDA call), with rot_last_error() set to its description: 0 -> ROT_OK;
+ * 1 (a dependency wait ran out) and 2 (a tile-copy wait ran out) ->
+ * ROT_ETIMEOUT; 3 (a work item decoded outside the problem, an internal
+ * error), 4 (cancelled) and any other code -> ROT_ECUDA.  The paper has no
+ * counterpart.
+ */
+rot_status rot_device_code_status(int code);
 
 #ifdef __cplusplus
 }

@@ -29,15 +29,18 @@ SIGNATURES = {
     "rot_apply": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_f32": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_device_status": (ci, []),
+    "rot_device_code_status": (ci, [ci]),
     "rot_selftest_wait_timeout": (ci, [ci, vp]),
     "rot_apply_host": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_reflectors": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_left": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_noalloc": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "rot_apply_noalloc_prepare": (ci, []),
     "rot_trace_start": (ci, []),
     "rot_trace_stop": (ci, [vp, ci, ctypes.POINTER(ci)]),
     "rot_launch_count": (ctypes.c_int64, []),
     "rot_measure_fp64_peak": (ci, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "rot_measure_fp64_mix": (ci, [ci, ci, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "rot_measure_tc_issue": (ci, [ci, ci, ci, ci, ctypes.POINTER(ctypes.c_double)]),
     "rot_batch_plan_create": (ci, [ci, vp, vp, ctypes.POINTER(vp)]),
     "rot_batch_plan_execute": (ci, [vp, vp]),
@@ -58,6 +61,7 @@ SIGNATURES = {
     "rot_server_register": (ci, [vp, i64, i64, vp, i64, ctypes.POINTER(ci)]),
     "rot_server_submit": (ci, [vp, ci, i64, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_uint64)]),
     "rot_server_wait": (ci, [vp, ctypes.c_uint64, ci]),
+    "rot_server_wait_latency": (ci, [vp, ctypes.c_uint64, ci, ctypes.POINTER(ctypes.c_double)]),
     "rot_server_stats": (ci, [vp, vp, ci]),
     "rot_server_destroy": (ci, [vp]),
 }

@@ -134,6 +134,22 @@ def measure_fp64_peak():
     return g.value, ms.value
 
 
+FP64_MIX_KINDS = {"dfma": 0, "dmul": 1, "rotation": 2, "rotation_smem": 3}
+
+
+def measure_fp64_mix(kind, warps_per_cta, ctas_per_sm):
+    """(FP64 lane-operations per second, ms per probe launch) of one register-only
+    instruction mix ('dfma', 'dmul', 'rotation', 'rotation_smem') at the given
+    launch shape on the current device."""
+    import ctypes
+    r = ctypes.c_double(0)
+    ms = ctypes.c_double(0)
+    _native.check(_native.load().rot_measure_fp64_mix(FP64_MIX_KINDS[kind], int(warps_per_cta),
+                                                      int(ctas_per_sm), ctypes.byref(r),
+                                                      ctypes.byref(ms)), "rot_measure_fp64_mix")
+    return r.value, ms.value
+
+
 def measure_tc_issue(m, n, accumulators, mmas=3000):
     """Mean ns per tcgen05.mma of shape m x n x 16 (BF16) over `accumulators`
     independent accumulators, one issuing thread per SM."""
@@ -306,6 +322,14 @@ class Server:
 
     def wait(self, ticket, timeout_ms=-1):
         _native.check(self._lib.rot_server_wait(self._h, int(ticket), int(timeout_ms)), "rot_server_wait")
+
+    def wait_latency(self, ticket, timeout_ms=-1):
+        """wait(); returns the request's submit-to-completion latency in ms."""
+        import ctypes
+        ms = ctypes.c_double(0)
+        _native.check(self._lib.rot_server_wait_latency(self._h, int(ticket), int(timeout_ms), ctypes.byref(ms)),
+                      "rot_server_wait_latency")
+        return ms.value
 
     def try_wait(self, ticket, timeout_ms=0):
         """Status code of the wait (0 = done and ok) instead of raising."""

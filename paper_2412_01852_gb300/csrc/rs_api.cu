@@ -1,6 +1,7 @@
 // rs_api.cu -- the extern "C" entry points declared in include/rotseq.h:
 // argument validation, quick returns, dispatch to the kernels.
 #include <cstdint>
+#include <cstdio>
 #include <cuda_runtime.h>
 #include "rs_internal.h"
 #include "rs_device.cuh"
@@ -98,14 +99,42 @@ rot_status rot_selftest_wait_timeout(int wait_ms, void* stream) {
   int dev_status = 0;
   const rot_status st = rs::selftest_dependency_timeout(wait_ms, static_cast<cudaStream_t>(stream), &dev_status);
   if (st != ROT_OK) return st;
-  return dev_status == rs::kDevTimeoutDependency ? ROT_ETIMEOUT : ROT_ECUDA;
+  return dev_status == rs::kDevTimeoutDependency ? rot_device_code_status(dev_status) : ROT_ECUDA;
 }
 
 rot_status rot_device_status(void) {
-  if (cudaDeviceSynchronize() != cudaSuccess) return ROT_ECUDA;
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return rs::cuda_failed(e, "rot_device_status: cudaDeviceSynchronize");
   const int s = rs::take_sticky_status();
-  if (s < 0) return ROT_ECUDA;
-  return s == 0 ? ROT_OK : ROT_ETIMEOUT;
+  if (s < 0) {
+    rs::note_error("rot_device_status: reading the sticky device status failed");
+    return ROT_ECUDA;
+  }
+  return rot_device_code_status(s);
+}
+
+rot_status rot_device_code_status(int code) {
+  switch (code) {
+    case rs::kDevOk: return ROT_OK;
+    case rs::kDevTimeoutDependency:
+      rs::note_error("device: a wait on another work item's progress ran out");
+      return ROT_ETIMEOUT;
+    case rs::kDevTimeoutTma:
+      rs::note_error("device: a wait on a (c,s) tile copy ran out");
+      return ROT_ETIMEOUT;
+    case rs::kDevBadItem:
+      rs::note_error("device: a work item decoded outside the problem (internal error)");
+      return ROT_ECUDA;
+    case rs::kDevCancelled:
+      rs::note_error("device: the launch was cancelled by the host");
+      return ROT_ECUDA;
+    default: {
+      char buf[96];
+      snprintf(buf, sizeof buf, "device: unknown status code %d", code);
+      rs::note_error(buf);
+      return ROT_ECUDA;
+    }
+  }
 }
 
 }  // extern "C"

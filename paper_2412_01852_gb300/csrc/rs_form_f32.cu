@@ -187,7 +187,11 @@ rot_status form32_enqueue(int64_t n, int64_t k, const double* C, int64_t ldc, co
   form32_table_kernel<<<tg, tb, 0, s>>>(C, ldc, S, lds, (int)n, (int)k, nb, kb, F.NT, F.KS, tab, c0s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_failed(e, "form_blocks_f32: table kernel");
-  const int tr = trace_begin(ROT_KERNEL_FORM_BLOCKS, F.nblk * (int64_t)F.L * nb * kb, s);
+  // Executed work: every warp of rows r0 .. r0+7 (r0 < L) runs steps
+  // r0 .. NT-1 of all KS stages on its 8 rows, padding stages included.
+  long long executed = 0;
+  for (int r0 = 0; r0 < F.L; r0 += kRows) executed += (long long)(F.NT - r0) * F.KS * kRows;
+  const int tr = trace_begin(ROT_KERNEL_FORM_BLOCKS, executed * F.nblk, s);
   switch (F.spl) {
     case 1: e = launch_form32<1>(tab, F, Q, s); break;
     case 2: e = launch_form32<2>(tab, F, Q, s); break;

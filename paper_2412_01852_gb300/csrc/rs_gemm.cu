@@ -502,11 +502,38 @@ struct FormLayout {
   std::vector<WaveSegment> seg;
   size_t done_ints = 0;
   long long tickets = 0;
+  long long executed_rows = 0;   // rotation-row updates the formation kernel executes
   // workspace offsets
   size_t o_cs = 0, o_tmap = 0, o_inst = 0, o_seg = 0, o_cnt = 0, cnt_bytes = 0, o_c0 = 0, total = 0;
   int64_t W2 = 0;
   int cs_rows = 0;
 };
+
+// Rotation-row updates that run_item executes for one formation instance
+// (rows < m only): the same wave and rotation bounds as the kernel, including
+// the waves it skips because a chain's rows are still zero there.
+static long long executed_rotation_rows(const WaveInstance& I) {
+  long long total = 0;
+  for (int c = 0; c < I.nchains; ++c) {
+    const int rows = std::min(32, I.m - 32 * c);
+    long long per_row = 0;
+    for (int g = 0; g < I.G; ++g) {
+      const int p0 = g * I.K;
+      const int kr = std::min(I.K, I.k - p0);
+      const int nw = I.n + kr - 2;
+      int wr_lo = I.W_lo - p0;
+      const int wr_hi = I.W_hi - p0;
+      if (I.unit_rows) wr_lo = std::max(wr_lo, c * 32 - p0 - 2);
+      for (int w = std::max(0, wr_lo); w < std::min(nw, wr_hi); ++w) {
+        const int l_lo = std::max(0, w - I.j_hi);
+        const int l_hi = std::min(kr - 1, w - I.j_lo);
+        if (l_hi >= l_lo) per_row += l_hi - l_lo + 1;
+      }
+    }
+    total += per_row * rows;
+  }
+  return total;
+}
 
 static void form_layout(int64_t n, int64_t k, int nb, int kb, FormLayout* F) {
   F->blocks = block_schedule(n, k, nb, kb);
@@ -529,6 +556,7 @@ static void form_layout(int64_t n, int64_t k, int nb, int kb, FormLayout* F) {
     I.W_lo = kb - 1;
     I.W_hi = kb - 1 + nb;
     I.unit_rows = 1;
+    F->executed_rows += executed_rotation_rows(I);
     F->inst.push_back(I);
     F->wp.push_back(pl);
     max_key = std::max(max_key, (pl.B - 1) + pl.delta * (pl.G - 1));
@@ -624,7 +652,7 @@ static rot_status form_blocks_enqueue(int64_t n, int64_t k, const double* C, int
   B.tuning.fp64_products = 1;  // identity rows are mostly zeros: keep the products on DMUL
   rot_status st = batch_prepare(&B);
   if (st != ROT_OK) return st;
-  st = batch_launch_kernel(B, s, ROT_KERNEL_FORM_BLOCKS, (long long)ni * L * nb * kb);
+  st = batch_launch_kernel(B, s, ROT_KERNEL_FORM_BLOCKS, F.executed_rows);
   if (st != ROT_OK) return st;
   count_launches(2);
   return ROT_OK;

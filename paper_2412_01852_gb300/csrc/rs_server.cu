@@ -157,7 +157,8 @@ void CUDART_CB on_launch_done(void* p) {
     std::lock_guard<std::mutex> lk(S->mu);
     for (auto& r : L->reqs) {
       r->t_done = t;
-      r->status = st == 0 ? ROT_OK : ROT_ETIMEOUT;
+      r->status = st == kDevOk ? ROT_OK
+                  : (st == kDevTimeoutDependency || st == kDevTimeoutTma) ? ROT_ETIMEOUT : ROT_ECUDA;
       r->done = true;
       S->latencies.push_back(t - r->t_submit);
       S->completed += 1;
@@ -486,6 +487,10 @@ rot_status rot_server_submit(rot_server* srv, int handle, int64_t k, const doubl
 }
 
 rot_status rot_server_wait(rot_server* srv, uint64_t ticket, int timeout_ms) {
+  return rot_server_wait_latency(srv, ticket, timeout_ms, nullptr);
+}
+
+rot_status rot_server_wait_latency(rot_server* srv, uint64_t ticket, int timeout_ms, double* latency_ms) {
   if (!srv) return ROT_EINVAL;
   rs::Server& S = srv->s;
   std::unique_lock<std::mutex> lk(S.mu);
@@ -496,6 +501,7 @@ rot_status rot_server_wait(rot_server* srv, uint64_t ticket, int timeout_ms) {
   if (timeout_ms < 0) S.cv_done.wait(lk, pred);
   else if (!S.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) return ROT_ETIMEOUT;
   S.live.erase(ticket);
+  if (latency_ms) *latency_ms = 1e3 * (r->t_done - r->t_submit);
   return (rot_status)r->status;
 }
 

@@ -81,6 +81,64 @@ __global__ void dfma_probe_kernel(double* out, double b, double c, int iters) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// FP64 instruction-mix probe: every thread keeps NP independent (x, y) pairs
+// in registers and updates each pair per iteration with
+//   KIND 0: two DFMA      x = fma(x, c, s), y = fma(y, c, s)
+//   KIND 1: two DMUL      x = x*c, y = y*c
+//   KIND 2: a rotation    2 DMUL + 2 DFMA with the wave kernel's placement
+//   KIND 3: a rotation whose (c, s) pair comes from shared memory (one
+//           broadcast 16-byte load per rotation, as in the wave kernel)
+// Values stay bounded: |c| < 1 and the rotation is orthogonal.  c and s pass
+// through an opaque move so that they sit in registers (an FP64 instruction
+// that reads a kernel parameter straight from the constant bank issues more
+// slowly, which would make the probe a poor ceiling).
+template <int KIND, int NP>
+__global__ void fp64_mix_probe_kernel(double* out, double c_arg, double s_arg, int iters) {
+  double c, s;
+  asm volatile("mov.b64 %0, %1;" : "=d"(c) : "d"(c_arg));
+  asm volatile("mov.b64 %0, %1;" : "=d"(s) : "d"(s_arg));
+  __shared__ double2 tab[64];
+  if (KIND == 3) {
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = make_double2(c, s * (1.0 - 1e-9 * i));
+    __syncthreads();
+  }
+  double x[NP], y[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    x[i] = 1.0 + threadIdx.x * 1e-9 + i * 1e-7;
+    y[i] = 0.5 - threadIdx.x * 1e-9 + i * 1e-7;
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      if constexpr (KIND == 0) {
+        x[i] = __fma_rn(x[i], c, s);
+        y[i] = __fma_rn(y[i], c, s);
+      } else if constexpr (KIND == 1) {
+        x[i] = __dmul_rn(x[i], c);
+        y[i] = __dmul_rn(y[i], c);
+      } else if constexpr (KIND == 2) {
+        const double sy = __dmul_rn(s, y[i]);
+        const double sx = __dmul_rn(s, x[i]);
+        const double xn = __fma_rn(c, x[i], sy);
+        y[i] = __fma_rn(c, y[i], -sx);
+        x[i] = xn;
+      } else {
+        const double2 cs = tab[(it * NP + i) & 63];
+        const double sy = __dmul_rn(cs.y, y[i]);
+        const double sx = __dmul_rn(cs.y, x[i]);
+        const double xn = __fma_rn(cs.x, x[i], sy);
+        y[i] = __fma_rn(cs.x, y[i], -sx);
+        x[i] = xn;
+      }
+    }
+  }
+  double acc = 0;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) acc += x[i] + y[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 }  // namespace rs
 
 extern "C" {
@@ -157,5 +215,58 @@ rot_status rot_measure_fp64_peak(double* gflops, double* ms_out) {
   return ROT_OK;
 }
 
+
+rot_status rot_measure_fp64_mix(int kind, int warps_per_cta, int ctas_per_sm, double* lane_ops_per_s,
+                                double* ms_out) {
+  if (!lane_ops_per_s || kind < 0 || kind > 3 || warps_per_cta < 1 || warps_per_cta > 32 ||
+      ctas_per_sm < 1 || ctas_per_sm > 32 || warps_per_cta * ctas_per_sm > 64)
+    return ROT_EINVAL;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rs::cuda_failed(e, "fp64 mix probe: cudaGetDevice");
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return rs::cuda_failed(e, "fp64 mix probe: cudaDeviceGetAttribute");
+  constexpr int NP = 4;
+  const int threads = warps_per_cta * 32;
+  const int blocks = nsm * ctas_per_sm;
+  // About 16 ms per launch at 2 FP64 lanes per clock per SM and 2 GHz.
+  const double lanes_per_iter = (double)NP * (kind >= 2 ? 4 : 2);
+  int iters = (int)(2.0e9 * 0.016 * 2.0 / (warps_per_cta * ctas_per_sm * 32.0 * lanes_per_iter));
+  if (iters < 16) iters = 16;
+  using K = void (*)(double*, double, double, int);
+  const K kernels[4] = {rs::fp64_mix_probe_kernel<0, NP>, rs::fp64_mix_probe_kernel<1, NP>,
+                        rs::fp64_mix_probe_kernel<2, NP>, rs::fp64_mix_probe_kernel<3, NP>};
+  double* buf = nullptr;
+  e = cudaMalloc(&buf, sizeof(double) * blocks * threads);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ROT_ENOMEM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rot_status st = ROT_OK;
+  float ms = 0.f;
+  const int reps = 3;
+  const double c = 0.99999999, s = 1.4142135e-4;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    st = rs::cuda_failed(e, "fp64 mix probe: cudaEventCreate");
+  } else {
+    kernels[kind]<<<blocks, threads>>>(buf, c, s, iters);
+    cudaEventRecord(e0);
+    for (int r = 0; r < reps; ++r) kernels[kind]<<<blocks, threads>>>(buf, c, s, iters);
+    cudaEventRecord(e1);
+    if ((e = cudaGetLastError()) != cudaSuccess) st = rs::cuda_failed(e, "fp64 mix probe: launch");
+    else if ((e = cudaEventSynchronize(e1)) != cudaSuccess || (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+      st = rs::cuda_failed(e, "fp64 mix probe: events");
+    rs::count_launches(reps + 1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (st != ROT_OK) return st;
+  const double lane_ops = (double)blocks * threads * iters * lanes_per_iter * reps;
+  *lane_ops_per_s = lane_ops / (ms * 1e-3);
+  if (ms_out) *ms_out = ms / reps;
+  return ROT_OK;
+}
 
 }  // extern "C"

@@ -86,6 +86,7 @@ def test_server_argument_checks_without_device(lib):
     t = ctypes.c_uint64()
     assert lib.rot_server_submit(None, 0, 4, None, 1, None, 1, ctypes.byref(t)) == 1
     assert lib.rot_server_wait(None, 1, 0) == 1
+    assert lib.rot_server_wait_latency(None, 1, 0, None) == 1
     assert lib.rot_server_destroy(None) == 0
 
 
@@ -144,3 +145,25 @@ def test_workspace_size_queries_are_host_only(lib):
     assert sz.value > 0
     assert lib.rot_batched_workspace_size(0, None, ctypes.byref(sz)) == 0 and sz.value == 0
     assert lib.rot_apply_batched_ws(2, ctypes.cast(arr, ctypes.c_void_p), P, 16, None) == 1
+
+
+def test_device_codes_map_to_distinct_statuses(lib):
+    """A device status word maps to ROT_ETIMEOUT only for the bounded waits;
+    an internal error (a work item decoded outside the problem) is ROT_ECUDA
+    and rot_last_error() names it."""
+    assert lib.rot_device_code_status(0) == 0
+    assert lib.rot_device_code_status(1) == 4
+    assert b"wait" in lib.rot_last_error()
+    assert lib.rot_device_code_status(2) == 4
+    assert lib.rot_device_code_status(3) == 2
+    assert b"work item" in lib.rot_last_error()
+    assert lib.rot_device_code_status(4) == 2
+    assert lib.rot_device_code_status(99) == 2
+    assert b"99" in lib.rot_last_error()
+
+
+def test_fp64_mix_probe_argument_checks_without_device(lib):
+    d = ctypes.c_double(0)
+    for args in [(-1, 8, 1), (4, 8, 1), (0, 0, 1), (0, 33, 1), (0, 8, 0), (0, 32, 3)]:
+        assert lib.rot_measure_fp64_mix(*args, ctypes.byref(d), None) == 1, args
+    assert lib.rot_measure_fp64_mix(0, 8, 2, None, None) == 1
