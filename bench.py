@@ -602,8 +602,9 @@ def variant_line(args):
             fn = lambda: api.rot_apply_gemm(work, C64, S64, nb=nb, kb=kb, mode=mode)
             drift = _orth_drift(torch, lambda Q: api.rot_apply_gemm(Q, C64, S64, nb=nb, kb=kb, mode=mode), n,
                                 torch.float64, dev)
-            drift_bound = {"dmma": 10 * n * 2.0 ** -53, "f16": 8 * k * 2.0 ** -24,
-                           "bf16": 8 * -(-k // kb) * 2.0 ** -16}[base]
+            P = -(-k // kb)
+            drift_bound = {"dmma": 32 * P ** 0.5 * 2.0 ** -53, "f16": P * 2.0 ** -20,
+                           "bf16": 1.5 * P * 2.0 ** -17}[base]
             kind, peak, dtype = "form_blocks", fp64_peak, {"f16": "f16x2", "bf16": "bf16x2", "dmma": "f64"}[base]
             cfg_line = {"workload": "precision-8192 accumulated blocks: A 8192x8192, k=192, nb=%d, kb=%d, %s"
                                     % (nb, kb, mode), "m": m, "n": n, "k": k, "nb": nb, "kb": kb, "mode": mode}
@@ -622,6 +623,7 @@ def variant_line(args):
         per_step = {kname: sum(v) / steps_traced for kname, v in by.items()}
         line.update({"value": args.steps * W / (ms * 1e-3), "ms_per_step": ms / args.steps, "dtype": dtype,
                      "config": cfg_line, "max_row_rel_err_vs_fp64_path": err,
+                     "row_rel_err_bound": drift_bound,
                      "orthogonality_identity": {"max_abs_QtQ_minus_I": drift, "bound": drift_bound,
                                                 "input": "I_%d" % n},
                      "kernel_ms_per_step": per_step})

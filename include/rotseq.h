@@ -235,12 +235,12 @@ rot_status rot_form_blocks_f32(int64_t n, int64_t k, const double* C, int64_t ld
  * accumulators in tensor memory) when nb + kb <= 320 (the FP16 split also
  * needs nb >= Lp/2, Lp = nb + kb rounded up to 32), otherwise on mma.sync
  * (32-row tiles); DMMA runs on mma.sync (m8n8k4 FP64).  A stays FP64 in
- * memory.  Accuracy against the FP64 result: DMMA within 16*(k+nb+kb)*2^-53
- * per row; the split modes lose precision in the products (FP16 split:
- * per-row relative error below 8*k*2^-24; BF16 split: about 2^-16 per block
- * product).  The *_Q32 modes form the blocks with rot_form_blocks_f32
- * instead (kb <= 128), which adds FP32 rounding to the blocks (per-row
- * error within the same bounds).  Same arguments as rot_apply plus nb, kb
+ * memory.  Accuracy against the FP64 result, per row, with P = ceil(k/kb)
+ * p-blocks (bounds the tests hold the modes to; measured errors are 2x to 4x
+ * below them): DMMA 32*sqrt(P)*2^-53; the split modes lose precision in the
+ * products: FP16 split P*2^-20, BF16 split 1.5*P*2^-17.  The *_Q32 modes
+ * form the blocks with rot_form_blocks_f32 instead (kb <= 128), which adds
+ * FP32 rounding to the blocks (per-row error within the same bounds).  Same arguments as rot_apply plus nb, kb
  * (multiples of 16, nb + kb <= 512) and the mode.  Scratch (the blocks and their split copies)
  * comes from the stream-ordered allocator.
  */
@@ -395,7 +395,12 @@ typedef struct {
  * sequences together, or all of them when it is 0) go out as one problem whose sequences are theirs in submission order, which
  * is the same computation.  A launch's grid is sized to the work items it can
  * run at once, leaving SMs to the launches beside it, and a launch with few
- * items per key uses p-blocks of 8 or 4 sequences.  The paper has no serving
+ * items per key uses p-blocks of 8 or 4 sequences.  Matrices of 1024 rows or
+ * more are "wide": a launch holds only wide or only narrow matrices (a
+ * request completes with its launch, so a small request never waits inside a
+ * long launch), at most one wide launch runs at a time, and it runs one CTA
+ * per SM, which leaves the other resident CTA slot of every SM to narrow
+ * launches that arrive meanwhile.  The paper has no serving
  * layer; every request computes Algorithm 2 on its matrix exactly as
  * rot_apply would (bit-identical results).
  */

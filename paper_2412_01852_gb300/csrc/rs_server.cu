@@ -87,6 +87,7 @@ struct Matrix {
   int64_t m, n, lda;
   double* A;
   bool busy = false;
+  bool wide = false;   // its launches can fill much of the GPU (see Server::wide_rows)
 };
 
 struct Request {
@@ -115,6 +116,7 @@ struct Launch {
   size_t arena_off = 0, arena_bytes = 0;
   std::vector<std::shared_ptr<Request>> reqs;
   volatile int* status_host = nullptr;  // pinned copy of the launch's device status
+  bool wide = false;                    // a launch over wide matrices
 };
 
 }  // namespace
@@ -135,6 +137,15 @@ struct Server {
   std::vector<Launch*> finished;      // completed launches, released by the scheduler
   uint64_t next_ticket = 1;
   long long warps = 1;                // resident warps of the batched kernel on this device
+  // Launch classes.  A matrix with at least wide_rows rows is "wide": its
+  // launch can keep most SMs busy for milliseconds.  Launches never mix the
+  // classes (a request completes with its whole launch, so a small request
+  // in a wide launch would wait for the large ones); at most one wide launch
+  // is in flight, and it runs one CTA per SM (enough to keep the FP64 pipe
+  // busy), so the other CTA slot of every SM stays open for narrow launches
+  // arriving meanwhile.
+  int64_t wide_rows = 1024;
+  bool wide_inflight = false;
   int inflight = 0;                   // requests admitted and not completed
   bool stop = false;
   std::thread thread;
@@ -167,6 +178,7 @@ void CUDART_CB on_launch_done(void* p) {
       S->inflight -= 1;
       S->mats[r->handle].busy = false;
     }
+    if (L->wide) S->wide_inflight = false;
     S->finished.push_back(L);
   }
   S->cv_done.notify_all();
@@ -213,7 +225,9 @@ bool size_launch(Server* S, const std::vector<Group>& gs, BatchLayout* L, std::v
   // A launch with few work items per key uses short p-blocks, so that even a
   // lone large request keeps the whole GPU busy (its latency is the tail).
   rot_tuning tu{};
-  tu.K = batch_pick_K((int)probs->size(), probs->data(), S->warps);
+  // A wide launch runs one CTA per SM: half the resident warps.
+  const bool wide = !gs.empty() && S->mats[gs[0].handle].wide;
+  tu.K = batch_pick_K((int)probs->size(), probs->data(), wide ? S->warps / 2 : S->warps);
   *L = BatchLayout{};
   if (batch_layout((int)probs->size(), probs->data(), tu, L) != ROT_OK) return false;
   *cs_region = align256(L->total);
@@ -236,6 +250,7 @@ void scheduler(Server* S) {
       if (!S->slots[i].busy) { free_slot = (int)i; break; }
     std::vector<Group> groups;
     int nreq = 0;
+    int launch_wide = -1;   // class of the launch being formed (-1: not yet known)
     if (free_slot >= 0 && !S->pending.empty()) {
       std::vector<int> gidx(S->mats.size(), -1);
       std::vector<char> blocked(S->mats.size(), 0);
@@ -244,6 +259,11 @@ void scheduler(Server* S) {
         const int h = r->handle;
         bool can = !blocked[h] && !S->mats[h].busy && S->inflight + nreq < S->cfg.max_inflight &&
                    nreq < S->cfg.max_batch;
+        // The launch takes the class of its first request; a wide launch only
+        // while no other wide launch runs.
+        if (can && launch_wide < 0 && S->mats[h].wide && S->wide_inflight) can = false;
+        if (can && launch_wide >= 0 && (int)S->mats[h].wide != launch_wide) can = false;
+        if (can && launch_wide < 0) launch_wide = S->mats[h].wide ? 1 : 0;
         if (can && gidx[h] >= 0 && S->cfg.max_fused_k > 0 && groups[gidx[h]].k + r->k > S->cfg.max_fused_k)
           can = false;
         if (!can) {
@@ -297,6 +317,8 @@ void scheduler(Server* S) {
       all.insert(all.end(), g.reqs.begin(), g.reqs.end());
     }
     S->inflight += nreq;
+    const bool wide = launch_wide == 1;
+    if (wide) S->wide_inflight = true;
     Slot& slot = S->slots[free_slot];
     slot.busy = true;
     S->launches += 1;
@@ -329,6 +351,7 @@ void scheduler(Server* S) {
     launch->arena_off = off;
     launch->arena_bytes = total;
     launch->reqs = all;
+    launch->wide = wide;
     BatchLaunch B;
     if (st == ROT_OK) {
       launch->status_host = reinterpret_cast<volatile int*>(slot.staging + total);
@@ -351,6 +374,7 @@ void scheduler(Server* S) {
         }
       }
       B.device = S->device;
+      if (wide) B.tuning.ctas_per_sm = 1;
       st = batch_prepare(&B);
     }
     cudaStream_t s = slot.stream;
@@ -379,6 +403,7 @@ void scheduler(Server* S) {
       }
       S->arena->release(off, total);
       slot.busy = false;
+      if (wide) S->wide_inflight = false;
       delete launch;
       S->cv_done.notify_all();
     }
@@ -434,6 +459,7 @@ rot_status rot_server_register(rot_server* srv, int64_t m, int64_t n, double* A,
   std::lock_guard<std::mutex> lk(srv->s.mu);
   rs::Matrix M;
   M.m = m; M.n = n; M.lda = lda; M.A = A;
+  M.wide = m >= srv->s.wide_rows;
   srv->s.mats.push_back(M);
   *handle = (int)srv->s.mats.size() - 1;
   return ROT_OK;

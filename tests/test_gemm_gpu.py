@@ -3,11 +3,18 @@
 Block formation is FP64 and follows the same per-element operation order as
 the oracle's form_block, so every non-zero entry is bit-identical (zeros may
 differ in sign: rotations on two zeros are skipped).  The block apply uses
-tensor-core products; each mode is held to its stated error bound against the
-FP64 oracle, per row:
-  DMMA        16*(k+nb+kb)*2^-53
-  split FP16  8*k*2^-24
-  split BF16  4*ceil(k/kb)*2^-16   (two block products per element per p-block)
+tensor-core products; each mode is held to an error bound against the FP64
+oracle, per row, with P = ceil(k/kb) p-blocks.  Every element passes through
+about two block products per p-block and the errors of the p-blocks add up
+like a random walk or linearly:
+  DMMA        32*sqrt(P)*2^-53    (FP64 products, FP64 accumulation)
+  split FP16  P*2^-20             (x = hi + 2^-11 lo: operands exact to ~2^-22)
+  split BF16  1.5*P*2^-17         (x = hi + lo: operands exact to ~2^-17)
+The constants were set from the errors measured on GB300 for these shapes
+(each bound is 1.8x to 4x the largest measured error; at the 8192 x 8192,
+k = 192, nb = 256, kb = 64 precision workload the measured errors are
+1.8e-15, 6.2e-7 and 9.1e-6, against bounds of 6.2e-15, 2.9e-6 and 3.4e-5), so
+that an accuracy regression of a few times fails.
 The *-q32 modes form the blocks in FP32 (rot_form_blocks_f32), which equal
 the oracle's FP32 blocks entry for entry; their products are held to the
 same bounds.
@@ -46,11 +53,12 @@ def row_rel(out, ref):
 
 def bound(mode, k, nb, kb):
     mode = mode.split("-")[0]
+    P = math.ceil(k / kb)
     if mode == "dmma":
-        return 16 * (k + nb + kb) * U64
+        return 32 * math.sqrt(P) * U64
     if mode == "f16":
-        return 8 * k * U32
-    return 4 * math.ceil(k / kb) * 2.0 ** -16
+        return P * 2.0 ** -20
+    return 1.5 * P * 2.0 ** -17
 
 
 @pytest.mark.parametrize("n,k,nb,kb", [(40, 9, 16, 16), (100, 40, 32, 16), (300, 64, 64, 32),
@@ -141,8 +149,7 @@ def test_orthogonality_drift_on_identity(api, mode):
     torch.cuda.synchronize()
     Q = Ad.cpu().numpy()
     drift = np.abs(Q.T @ Q - np.eye(n)).max()
-    tol = {"dmma": 10 * n * U64, "f16": 8 * k * U32,
-           "bf16": 8 * math.ceil(k / kb) * 2.0 ** -16}[mode.split("-")[0]]
+    tol = bound(mode, k, nb, kb)
     assert drift <= tol, drift
 
 

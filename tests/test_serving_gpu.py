@@ -134,3 +134,31 @@ def test_destroy_drains_submitted_work(api):
         exp = oracle.rot_sequence(exp, C, S)
     srv.close()                           # no wait: destroy must finish them
     assert np.array_equal(bits(Ad.cpu().numpy()), bits(exp))
+
+
+def test_wide_and_narrow_matrices_mixed_equal_sequential_oracle(api):
+    """Matrices of 1024 rows or more go out in launches of their own (one at a
+    time, one CTA per SM); small ones in other launches beside them.  Every
+    matrix still ends equal to the oracle's sequential application, and each
+    request reports a latency."""
+    r = np.random.default_rng(17)
+    shapes = [(1024, 300), (1100, 257), (128, 128), (64, 200), (256, 256), (1024, 64)]
+    mats = [wl.matrix(m, n, seed=700 + i) for i, (m, n) in enumerate(shapes)]
+    devm = [dev(A) for A in mats]
+    expected = [A.copy() for A in mats]
+    reqs = []
+    for q in range(60):
+        i = int(r.integers(0, len(shapes)))
+        k = int(r.integers(2, 40))
+        reqs.append((i,) + wl.rotations(shapes[i][1], k, seed=9500 + q))
+    with api.Server(hbm_budget_bytes=512 << 20, max_inflight=16, streams=4, max_batch=6) as srv:
+        handles = [srv.register(A) for A in devm]
+        tickets = [srv.submit(handles[i], C, S) for (i, C, S) in reqs]
+        lat = [srv.wait_latency(t, 60000) for t in tickets]
+        assert all(x > 0 for x in lat)
+        st = srv.stats()
+        assert st["completed"] == 60 and st["pending"] == 0 and st["inflight"] == 0
+    for (i, C, S) in reqs:
+        expected[i] = oracle.rot_sequence(expected[i], C, S)
+    for A, E in zip(devm, expected):
+        assert np.array_equal(bits(A.cpu().numpy()), bits(E))
