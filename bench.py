@@ -334,6 +334,8 @@ def main():
                     help="requests per offered-load level in the embedded serving measurement")
     ap.add_argument("--serve-batch", type=int, default=64, help="requests per launch in the serving variant")
     ap.add_argument("--serve-streams", type=int, default=8, help="server streams in the serving variant")
+    ap.add_argument("--serve-wide-rows", type=int, default=0,
+                    help="server's wide-matrix threshold in rows (0: the library default, 2048)")
     ap.add_argument("--serve-fuse-k", type=int, default=192,
                     help="most sequences fused per matrix per launch in the serving variant (0 = no limit)")
     args = ap.parse_args()
@@ -784,6 +786,37 @@ def variant_line(args):
             if hbm:
                 row["frac_of_measured_hbm"] = row["hbm_gbs"] / hbm
             rows.append(row)
+        # The same HBM-bound cases on the packed layout (32-row strips, each a
+        # contiguous 32 x n panel): same kernels, same bits, contiguous runs.
+        P32 = api.pack(A32)
+        P64 = api.pack(A64)
+        packed_rows = []
+        for prec, kk in (("f32", 1), ("f32", 2), ("f32", 4), ("f32", 8), ("f32", 16), ("f64", 1), ("f64", 2)):
+            C, S = wl.rotations(n, kk, cfg["seed"])
+            if prec == "f32":
+                Cd, Sd = (_dev_colmajor(torch, X.astype(np.float32), dev) for X in (C, S))
+                fn = lambda: api.rot_apply_packed(P32, m, n, Cd, Sd)
+                esz = 4
+            else:
+                Cd, Sd = (_dev_colmajor(torch, X, dev) for X in (C, S))
+                fn = lambda: api.rot_apply_packed(P64, m, n, Cd, Sd)
+                esz = 8
+            reps = max(args.steps, 10)
+            api.trace_start()
+            ms = timed_alone(fn, reps)
+            recs = api.trace_stop()
+            kern = [r[1] for r in recs if r[0] in ("wave_f32", "wave_f64")]
+            kms = sum(kern) / (3 + reps) if kern else ms
+            passes = -(-kk // 8)
+            nbytes = passes * 2 * m * n * esz + 2 * (n - 1) * kk * esz
+            col = next(r for r in rows if r["precision"] == prec and r["k"] == kk)
+            row = {"precision": prec, "k": kk, "layout": "packed", "ms": ms, "kernel_ms": kms,
+                   "hbm_gbs": nbytes / (kms * 1e-3) / 1e9, "column_major_kernel_ms": col["kernel_ms"],
+                   "speedup_vs_column_major": col["kernel_ms"] / kms}
+            if hbm:
+                row["frac_of_measured_hbm"] = row["hbm_gbs"] / hbm
+            packed_rows.append(row)
+        del P32, P64
         rs.rot_device_status()
         first = rows[0]
         line.update({"value": first["rot_rows_per_s"], "ms_per_step": first["ms"], "dtype": "f32",
@@ -792,6 +825,7 @@ def variant_line(args):
                                             "seed 2",
                                 "m": m, "n": n, "l2": "flushed before every timed run (256 MiB write)"},
                      "per_k": rows,
+                     "packed_layout": packed_rows,
                      "roofline": {"bound": "hbm", "kernel": "stream_kernel<float, 1> at k = 1",
                                   "kernel_ms": first["kernel_ms"],
                                   "achieved": first["hbm_gbs"], "peak": hbm, "unit": "GB/s",
@@ -875,7 +909,8 @@ def variant_line(args):
         per_size = 4
         mats, handles = [], {}
         srv = api.Server(hbm_budget_bytes=4 << 30, max_inflight=256, streams=args.serve_streams,
-                         max_batch=args.serve_batch, max_fused_k=args.serve_fuse_k)
+                         max_batch=args.serve_batch, max_fused_k=args.serve_fuse_k,
+                         wide_rows=args.serve_wide_rows)
         for s_i, nsz in enumerate(sizes):
             for j in range(per_size):
                 Ad = _dev_colmajor(torch, wl.matrix(nsz, nsz, seed=7000 + 10 * s_i + j), dev)
@@ -949,7 +984,8 @@ def variant_line(args):
                                             % len(mats), "requests_per_level": args.serve_requests,
                                 "server": {"hbm_budget_bytes": 4 << 30, "max_inflight": 256,
                                            "streams": args.serve_streams, "max_batch": args.serve_batch,
-                                           "max_fused_k": args.serve_fuse_k}},
+                                           "max_fused_k": args.serve_fuse_k,
+                                           "wide_rows": args.serve_wide_rows or 2048}},
                      "capacity": {"requests_per_s": cap_rps, "p50_ms": st_burst["p50_ms"],
                                   "p99_ms": st_burst["p99_ms"], "mean_batch": st_burst["mean_batch"]},
                      "alone_latency_idle_gpu": alone,

@@ -179,6 +179,45 @@ rot_status rot_apply_noalloc(int64_t m, int64_t n, int64_t k, double* A, int64_t
  * call fails (rot_last_error() names it).  The paper has no counterpart. */
 rot_status rot_apply_noalloc_prepare(void);
 
+/* ---- the packed resident layout (Section 4's pre-packed A, rs_kernel_v2) -- */
+
+/*
+ * Packed layout of an m x n matrix: ceil(m/32) strips of 32 rows, strip s a
+ * 32 x n column-major panel (leading dimension 32) holding rows 32s..32s+31,
+ * the strips one after the other:
+ *     P[(i/32)*32*n + j*32 + i%32] = A(i,j),
+ * rows past m in the last strip are zero.  A warp of the rotation kernels
+ * owns 32 rows and walks the columns, so in this layout it reads and writes
+ * one contiguous run of memory.  A matrix that stays on the device across
+ * many applications is packed once.
+ * rot_packed_elems: elements of the packed buffer, ceil(m/32)*32*n (-1 for
+ * negative or too large sizes).
+ */
+int64_t rot_packed_elems(int64_t m, int64_t n);
+
+/* Column-major A (lda >= max(1,m)) into packed P, and back (rot_unpack writes
+ * rows < m only).  Device pointers, asynchronous on `stream`; P holds
+ * rot_packed_elems(m, n) elements.  ROT_EINVAL for bad sizes or NULL
+ * pointers with work to do. */
+rot_status rot_pack(int64_t m, int64_t n, const double* A, int64_t lda, double* P, void* stream);
+rot_status rot_unpack(int64_t m, int64_t n, const double* P, double* A, int64_t lda, void* stream);
+rot_status rot_pack_f32(int64_t m, int64_t n, const float* A, int64_t lda, float* P, void* stream);
+rot_status rot_unpack_f32(int64_t m, int64_t n, const float* P, float* A, int64_t lda, void* stream);
+
+/*
+ * rot_apply / rot_apply_f32 on a packed matrix P (m x n): the same result bit
+ * for bit (rows are independent and each row sees the same operations).
+ * Few sequences (k <= 16 in FP64, k <= 48 in FP32, with m, n >= 64 and P
+ * 16-byte aligned) run the column stream over the strips; otherwise the
+ * wavefront kernel.  The lane pipelines that rot_apply uses for
+ * 3 <= k <= 32 (FP64) and k > 48 (FP32) are not used here, so those k run
+ * slower than on a column-major matrix.  Same error codes as rot_apply.
+ */
+rot_status rot_apply_packed(int64_t m, int64_t n, int64_t k, double* P, const double* C, int64_t ldc,
+                            const double* S, int64_t lds, void* stream);
+rot_status rot_apply_packed_f32(int64_t m, int64_t n, int64_t k, float* P, const float* C, int64_t ldc,
+                                const float* S, int64_t lds, void* stream);
+
 /* ---- accumulated blocks applied by matrix products (rs_gemm, Section 8) -- */
 
 typedef enum {
@@ -370,6 +409,9 @@ typedef struct {
   int max_batch;            /* requests per launch */
   int max_fused_k;          /* most sequences of queued requests on one matrix
                                fused into one problem; 0 = no limit */
+  int wide_rows;            /* matrices with at least this many rows are
+                               "wide" (see rot_server_create); 0 = 2048,
+                               negative = no matrix is wide */
 } rot_server_config;
 
 typedef struct {
@@ -395,12 +437,12 @@ typedef struct {
  * sequences together, or all of them when it is 0) go out as one problem whose sequences are theirs in submission order, which
  * is the same computation.  A launch's grid is sized to the work items it can
  * run at once, leaving SMs to the launches beside it, and a launch with few
- * items per key uses p-blocks of 8 or 4 sequences.  Matrices of 1024 rows or
- * more are "wide": a launch holds only wide or only narrow matrices (a
- * request completes with its launch, so a small request never waits inside a
- * long launch), at most one wide launch runs at a time, and it runs one CTA
- * per SM, which leaves the other resident CTA slot of every SM to narrow
- * launches that arrive meanwhile.  The paper has no serving
+ * items per key uses p-blocks of 8 or 4 sequences.  Matrices of
+ * cfg->wide_rows rows or more (2048 by default) are "wide": a launch holds
+ * only wide or only narrow matrices (a request completes with its launch, so
+ * a small request never waits inside a long launch), at most one wide launch
+ * runs at a time, and it runs one CTA per SM, which leaves the other resident
+ * CTA slot of every SM to narrow launches that arrive meanwhile.  The paper has no serving
  * layer; every request computes Algorithm 2 on its matrix exactly as
  * rot_apply would (bit-identical results).
  */

@@ -36,6 +36,13 @@ SIGNATURES = {
     "rot_apply_left": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_noalloc": (ci, [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]),
     "rot_apply_noalloc_prepare": (ci, []),
+    "rot_packed_elems": (i64, [i64, i64]),
+    "rot_pack": (ci, [i64, i64, vp, i64, vp, vp]),
+    "rot_unpack": (ci, [i64, i64, vp, vp, i64, vp]),
+    "rot_pack_f32": (ci, [i64, i64, vp, i64, vp, vp]),
+    "rot_unpack_f32": (ci, [i64, i64, vp, vp, i64, vp]),
+    "rot_apply_packed": (ci, [i64, i64, i64, vp, vp, i64, vp, i64, vp]),
+    "rot_apply_packed_f32": (ci, [i64, i64, i64, vp, vp, i64, vp, i64, vp]),
     "rot_trace_start": (ci, []),
     "rot_trace_stop": (ci, [vp, ci, ctypes.POINTER(ci)]),
     "rot_launch_count": (ctypes.c_int64, []),
@@ -69,7 +76,8 @@ SIGNATURES = {
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
-                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_fused_k", ctypes.c_int)]
+                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_fused_k", ctypes.c_int),
+                ("wide_rows", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):

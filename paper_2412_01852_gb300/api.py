@@ -78,6 +78,51 @@ def rot_apply_f32(A, C, S, stream=None):
     return A
 
 
+# ---- packed resident layout ------------------------------------------------------
+
+def packed_elems(m, n):
+    """Elements of the packed buffer of an m x n matrix (32-row strips)."""
+    return int(_native.load().rot_packed_elems(int(m), int(n)))
+
+
+def pack(A, stream=None):
+    """Column-major device tensor A (m x n) -> a new 1-D tensor in the packed
+    layout (strip s of 32 rows is a 32 x n column-major panel)."""
+    lib = _native.load()
+    m, n = A.shape
+    P = torch.empty(packed_elems(m, n), dtype=A.dtype, device=A.device)
+    fn = lib.rot_pack if A.dtype == torch.float64 else lib.rot_pack_f32
+    _native.check(fn(m, n, _ptr(A), _ld(A, m), _ptr(P), _stream_handle(stream)), "rot_pack")
+    return P
+
+
+def unpack(P, A, stream=None):
+    """Packed P into the column-major device tensor A (m x n), in place."""
+    lib = _native.load()
+    m, n = A.shape
+    if P.numel() < packed_elems(m, n) or P.dtype != A.dtype:
+        raise ValueError("P must hold packed_elems(m, n) elements of A's dtype")
+    fn = lib.rot_unpack if A.dtype == torch.float64 else lib.rot_unpack_f32
+    _native.check(fn(m, n, _ptr(P), _ptr(A), _ld(A, m), _stream_handle(stream)), "rot_unpack")
+    return A
+
+
+def rot_apply_packed(P, m, n, C, S, stream=None):
+    """rot_apply (FP64) or rot_apply_f32 (FP32, by P's dtype) on a packed matrix."""
+    lib = _native.load()
+    k = C.shape[1] if C.dim() == 2 else 0
+    if P.numel() < packed_elems(m, n):
+        raise ValueError("P must hold packed_elems(m, n) elements")
+    if not P.is_cuda or not C.is_cuda or not S.is_cuda:
+        raise ValueError("device tensors expected")
+    if C.dtype != P.dtype or S.dtype != P.dtype:
+        raise ValueError("C and S must have P's dtype")
+    fn = lib.rot_apply_packed if P.dtype == torch.float64 else lib.rot_apply_packed_f32
+    _native.check(fn(int(m), int(n), int(k), _ptr(P), _ptr(C), _ld(C, max(1, n - 1)), _ptr(S),
+                     _ld(S, max(1, n - 1)), _stream_handle(stream)), "rot_apply_packed")
+    return P
+
+
 def rot_device_status():
     """Synchronize; raise RotError if a kernel recorded a device-side failure."""
     lib = _native.load()
@@ -287,11 +332,12 @@ class Server:
     done (raises RotError on failure, including a wait that runs out).
     """
 
-    def __init__(self, hbm_budget_bytes=1 << 30, max_inflight=64, streams=4, max_batch=32, max_fused_k=192):
+    def __init__(self, hbm_budget_bytes=1 << 30, max_inflight=64, streams=4, max_batch=32, max_fused_k=192,
+                 wide_rows=0):
         import ctypes
         self._lib = _native.load()
         cfg = _native.ServerConfig(int(hbm_budget_bytes), int(max_inflight), int(streams), int(max_batch),
-                                   int(max_fused_k))
+                                   int(max_fused_k), int(wide_rows))
         h = ctypes.c_void_p()
         _native.check(self._lib.rot_server_create(ctypes.cast(ctypes.pointer(cfg), ctypes.c_void_p),
                                                   ctypes.byref(h)), "rot_server_create")

@@ -17,6 +17,7 @@ struct WaveOptions {
   const int* arrived = nullptr;  // upload progress flags per chunk of arrive_cols columns (FP64 only)
   int arrive_cols = 0;
   int* last_done = nullptr;      // per wave-block completion counts of the last p-block
+  int64_t chain_stride = 0;      // between 32-row strips (0: column-major; packed layout: 32 n)
 };
 
 // The FP64 products used when a caller leaves the choice to the library.
@@ -44,9 +45,10 @@ rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const 
 // takes this problem, and the call.
 template <typename T>
 bool stream_fits(int64_t m, int64_t n, int64_t k, const T* A, int64_t lda);
+// packed: A is in the packed layout (32-row strips; lda is ignored).
 template <typename T>
 rot_status stream_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
-                        const T* S, int64_t lds, cudaStream_t stream);
+                        const T* S, int64_t lds, cudaStream_t stream, bool packed = false);
 
 // Rotations as a pipeline of sequences across a warp's lanes (rs_pipe.cu):
 // whether it takes this problem, and the call (FP32: k >= 32; FP64:

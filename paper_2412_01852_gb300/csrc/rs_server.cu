@@ -14,6 +14,7 @@
 // also stamps the completion time used for latency statistics.
 #include <algorithm>
 #include <chrono>
+#include <cstdint>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -144,7 +145,7 @@ struct Server {
   // is in flight, and it runs one CTA per SM (enough to keep the FP64 pipe
   // busy), so the other CTA slot of every SM stays open for narrow launches
   // arriving meanwhile.
-  int64_t wide_rows = 1024;
+  int64_t wide_rows = 2048;           // rows from which a matrix is wide (rot_server_config)
   bool wide_inflight = false;
   int inflight = 0;                   // requests admitted and not completed
   bool stop = false;
@@ -429,6 +430,7 @@ rot_status rot_server_create(const rot_server_config* cfg, rot_server** out) {
   if (!h) return ROT_ENOMEM;
   rs::Server& S = h->s;
   S.cfg = *cfg;
+  S.wide_rows = cfg->wide_rows > 0 ? cfg->wide_rows : cfg->wide_rows < 0 ? INT64_MAX : 2048;
   if (cudaGetDevice(&S.device) != cudaSuccess) { delete h; return ROT_ECUDA; }
   void* a = nullptr;
   if (cudaMalloc(&a, cfg->hbm_budget_bytes) != cudaSuccess) { cudaGetLastError(); delete h; return ROT_ENOMEM; }

@@ -19,8 +19,9 @@ inline int64_t round_up256(int64_t x) { return (x + 255) / 256 * 256; }
 
 template <typename T, int KR>
 rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc, const T* S,
-                         int64_t lds, cudaStream_t s) {
+                         int64_t lds, cudaStream_t s, bool packed) {
   constexpr int R = stream_rows<T, KR>();
+  static_assert(R == 1, "the packed layout's strips are 32 rows");
   using SS = StreamShape<T, KR, R>;
   constexpr bool kF64 = sizeof(T) == 8;
   const int64_t W2 = 2 * SS::KP;                   // elements per (c,s) row
@@ -44,7 +45,11 @@ rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, con
     dim3 rg((unsigned)((n - 1 + 31) / 32), (unsigned)((k + 7) / 8));
     repack_cs_kernel<T><<<rg, rb, 0, s>>>(C, ldc, S, lds, (int)n, (int)k, cs, W2, 0);
     CUtensorMap amap, csmap;
-    if (!encode_tile_map_2d(&amap, A, kF64, (uint64_t)m, (uint64_t)n, (uint64_t)lda * sizeof(T), 32 * R, SS::CB) ||
+    // Packed: a tensor 32 elements wide with one row per (strip, column).
+    const uint64_t a_inner = packed ? 32 : (uint64_t)m;
+    const uint64_t a_outer = packed ? (uint64_t)((m + 31) / 32) * (uint64_t)n : (uint64_t)n;
+    const uint64_t a_pitch = packed ? 32 * sizeof(T) : (uint64_t)lda * sizeof(T);
+    if (!encode_tile_map_2d(&amap, A, kF64, a_inner, a_outer, a_pitch, 32 * R, SS::CB) ||
         !encode_tile_map_2d(&csmap, cs, kF64, (uint64_t)W2, (uint64_t)cs_rows, (uint64_t)W2 * sizeof(T),
                             (uint32_t)W2, SS::CB)) {
       note_error("stream: cuTensorMapEncodeTiled failed");
@@ -55,8 +60,9 @@ rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, con
     e = smem_opt_in(reinterpret_cast<const void*>(kfn), SS::kSmem);
     if (e != cudaSuccess) { st = cuda_failed(e, "stream: shared-memory opt-in"); break; }
     const int tr = trace_begin(kF64 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32, m * (n - 1) * k, s);
-    kfn<<<(unsigned)((m + 32 * R - 1) / (32 * R)), 32, SS::kSmem, s>>>(amap, csmap, A, lda, (int)m, (int)n, (int)k,
-                                                                       status);
+    kfn<<<(unsigned)((m + 32 * R - 1) / (32 * R)), 32, SS::kSmem, s>>>(amap, csmap, A, packed ? 32 : lda, (int)m,
+                                                                       (int)n, (int)k, status,
+                                                                       packed ? (int)n : 0);
     trace_end(tr, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) { st = cuda_failed(e, "stream: kernel launch"); break; }
@@ -81,16 +87,16 @@ bool stream_fits(int64_t m, int64_t n, int64_t k, const T* A, int64_t lda) {
 
 template <typename T>
 rot_status stream_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc, const T* S,
-                        int64_t lds, cudaStream_t s) {
+                        int64_t lds, cudaStream_t s, bool packed) {
   for (int64_t p0 = 0; p0 < k; p0 += 8) {
     const int64_t kk = std::min<int64_t>(8, k - p0);
     const T* Cp = C + p0 * ldc;
     const T* Sp = S + p0 * lds;
     rot_status st;
-    if (kk == 1) st = stream_launch<T, 1>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s);
-    else if (kk == 2) st = stream_launch<T, 2>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s);
-    else if (kk <= 4) st = stream_launch<T, 4>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s);
-    else st = stream_launch<T, 8>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s);
+    if (kk == 1) st = stream_launch<T, 1>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s, packed);
+    else if (kk == 2) st = stream_launch<T, 2>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s, packed);
+    else if (kk <= 4) st = stream_launch<T, 4>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s, packed);
+    else st = stream_launch<T, 8>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s, packed);
     if (st != ROT_OK) return st;
   }
   return ROT_OK;
@@ -99,8 +105,8 @@ rot_status stream_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, cons
 template bool stream_fits<double>(int64_t, int64_t, int64_t, const double*, int64_t);
 template bool stream_fits<float>(int64_t, int64_t, int64_t, const float*, int64_t);
 template rot_status stream_apply<double>(int64_t, int64_t, int64_t, double*, int64_t, const double*, int64_t,
-                                         const double*, int64_t, cudaStream_t);
+                                         const double*, int64_t, cudaStream_t, bool);
 template rot_status stream_apply<float>(int64_t, int64_t, int64_t, float*, int64_t, const float*, int64_t,
-                                        const float*, int64_t, cudaStream_t);
+                                        const float*, int64_t, cudaStream_t, bool);
 
 }  // namespace rs

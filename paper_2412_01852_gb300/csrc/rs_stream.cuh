@@ -87,7 +87,10 @@ __device__ __forceinline__ void stream_tile(T (&win)[R][KR + 1], const T* at, co
 template <typename T, int KR, int R>
 __global__ void __launch_bounds__(32)
 stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap csmap, T* A,
-              int64_t lda, int m, int n, int k, int* status) {
+              int64_t lda, int m, int n, int k, int* status, int packed_n) {
+  // packed_n != 0: A is in the packed layout (32-row strips, each a 32 x n
+  // column-major panel, one after the other; lda = 32, R = 1) and amap views
+  // it as a 32-wide tensor of strips * n rows.
   using SS = StreamShape<T, KR, R>;
   using V2 = typename Pair<T>::type;
   constexpr int U = SS::U, CB = SS::CB, S = SS::S;
@@ -99,7 +102,7 @@ stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
 #pragma unroll
   for (int r = 0; r < R; ++r) rowok[r] = c * 32 * R + r * 32 + lane < m;
   // Row of slot r: arow + 32r (only dereferenced where rowok[r]).
-  T* const arow = A + (int64_t)c * 32 * R + lane;
+  T* const arow = A + (packed_n ? (int64_t)c * 32 * packed_n : (int64_t)c * 32 * R) + lane;
   // Waves -1 .. n-2+KR: after the last one, column n-1 has been stored.
   const int ntiles = (n + KR + CB - 1) / CB;
   if (lane == 0) {
@@ -116,7 +119,8 @@ stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
     unsigned char* st = smem + s * SS::kStage;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&bar[s], SS::kABytes + SS::kCsBytes);
-    tma_load_2d(st, &amap, &bar[s], c * 32 * R, t * CB);
+    if (packed_n) tma_load_2d(st, &amap, &bar[s], 0, c * packed_n + t * CB);
+    else tma_load_2d(st, &amap, &bar[s], c * 32 * R, t * CB);
     tma_load_2d(st + SS::kAStage, &csmap, &bar[s], 0, t * CB - 1);
   };
   if (lane == 0)

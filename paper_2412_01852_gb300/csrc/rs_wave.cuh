@@ -160,6 +160,11 @@ enum WaveOp : int {
 struct WaveInstance {
   void* A;          // column-major m x n, leading dimension lda (elements)
   int64_t lda;
+  // Elements from row 0 of one 32-row strip to row 0 of the next: 0 means 32
+  // (plain column-major).  The packed layout (strips of 32 rows stored one
+  // after the other, each a 32 x n column-major panel) has lda = 32 and
+  // chain_stride = 32 n.
+  int64_t chain_stride;
   int m, n, k;
   int K;            // sequences per p-block
   int NB;           // waves per item
@@ -323,7 +328,7 @@ __device__ __forceinline__ bool run_item(const WaveInstance& I, const void* tmap
   // ---- load the window: columns [w0-kr+1, w0] owned by this p-block ---------
   const int row = c * 32 + lane;
   const bool rowok = row < I.m;
-  T* const arow = reinterpret_cast<T*>(I.A) + row;
+  T* const arow = reinterpret_cast<T*>(I.A) + (int64_t)c * (I.chain_stride ? I.chain_stride : 32) + lane;
   const int64_t lda = I.lda;
   const int own_lo = w0 - kr + 1;
   T win[KMAX + 1];

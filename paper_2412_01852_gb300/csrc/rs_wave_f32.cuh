@@ -54,6 +54,7 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
   if (!ok) return false;
 
   const int64_t lda = I.lda;
+  const int64_t cstr = I.chain_stride ? I.chain_stride : 32;   // between 32-row strips
   // Retired columns are read again by the next p-block about two items
   // later; storing them as evict_last keeps more of them in L2 (measured:
   // 2.5 % less time at 8192 x 8192, k = 192; the p-blocks in flight span
@@ -65,7 +66,7 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
   for (int r = 0; r < R; ++r) {
     const int row = c * (32 * R) + r * 32 + lane;
     rowok[r] = row < I.m;
-    arow[r] = reinterpret_cast<T*>(I.A) + row;
+    arow[r] = reinterpret_cast<T*>(I.A) + (int64_t)(c * R + r) * cstr + lane;
   }
   const int own_lo = w0 - kr + 1;
   // Columns enter the window one per wave (column w+1 at wave w).  At FP32
@@ -131,8 +132,8 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
       // one an edge tile takes from `pre`) is fetched.
       const bool next_whole = ws + 2 * U <= col_hi;
       const bool next_first = ws + U + 1 <= col_hi;
-      const T* pl = reinterpret_cast<const T*>(I.A) + (int64_t)(ws + U + 1) * lda + c * (32 * R) + lane;
-      T* ps = reinterpret_cast<T*>(I.A) + (int64_t)(ws + 1 - KMAX) * lda + c * (32 * R) + lane;
+      const T* pl = reinterpret_cast<const T*>(I.A) + (int64_t)(ws + U + 1) * lda + (int64_t)c * R * cstr + lane;
+      T* ps = reinterpret_cast<T*>(I.A) + (int64_t)(ws + 1 - KMAX) * lda + (int64_t)c * R * cstr + lane;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const bool fetch = u == 0 ? next_first : next_whole;
@@ -140,7 +141,7 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
         for (int r = 0; r < R; ++r) {
           win[r][(KMAX + u) % U] = pre[r][u];
           pre[r][u] = T(0);
-          if (fetch && rowok[r]) pre[r][u] = ld_cg(pl + r * 32);
+          if (fetch && rowok[r]) pre[r][u] = ld_cg(pl + r * cstr);
         }
         pl += lda;
         const V2* trow = tl + u * KMAX;
@@ -154,7 +155,7 @@ __device__ __forceinline__ bool run_item_f32(const WaveInstance& I, const void* 
         // column w + 1 - KMAX (>= own_lo and >= 0 in an interior tile) retires
 #pragma unroll
         for (int r = 0; r < R; ++r)
-          if (rowok[r]) st_l2_keep(ps + r * 32, win[r][u % U], keep);
+          if (rowok[r]) st_l2_keep(ps + r * cstr, win[r][u % U], keep);
         ps += lda;
       }
     } else {

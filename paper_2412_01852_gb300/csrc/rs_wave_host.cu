@@ -174,6 +174,7 @@ rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const 
     P.K = pl.K; P.NB = pl.NB; P.delta = pl.delta; P.nchains = pl.nchains; P.G = pl.G; P.B = pl.B;
     P.cs_row0 = 0;
     set_full_range(P);
+    P.chain_stride = opt.chain_stride;
     P.done = reinterpret_cast<int*>(base + done_off);
     P.ticket = reinterpret_cast<unsigned long long*>(base + tick_off);
     P.status = reinterpret_cast<int*>(base + tick_off + 64);
@@ -273,6 +274,7 @@ rot_status wave_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda
     P.K = pl.K; P.NB = pl.NB; P.delta = pl.delta; P.nchains = pl.nchains; P.G = pl.G; P.B = pl.B;
     P.cs_row0 = 0;
     set_full_range(P);
+    P.chain_stride = opt.chain_stride;
     P.done = reinterpret_cast<int*>(base + done_off);
     P.ticket = reinterpret_cast<unsigned long long*>(base + tick_off);
     P.status = reinterpret_cast<int*>(base + tick_off + 64);

@@ -167,3 +167,20 @@ def test_fp64_mix_probe_argument_checks_without_device(lib):
     for args in [(-1, 8, 1), (4, 8, 1), (0, 0, 1), (0, 33, 1), (0, 8, 0), (0, 32, 3)]:
         assert lib.rot_measure_fp64_mix(*args, ctypes.byref(d), None) == 1, args
     assert lib.rot_measure_fp64_mix(0, 8, 2, None, None) == 1
+
+
+def test_packed_layout_arguments_checked_on_the_host(lib):
+    """Sizes of the packed layout and argument checks before any device call."""
+    assert lib.rot_packed_elems(100, 7) == 128 * 7
+    assert lib.rot_packed_elems(32, 5) == 32 * 5
+    assert lib.rot_packed_elems(0, 5) == 0
+    assert lib.rot_packed_elems(-1, 5) == -1
+    assert lib.rot_pack(10, 4, P, 5, P, None) == 1          # lda < m
+    assert lib.rot_pack(10, 4, None, 10, P, None) == 1      # no A
+    assert lib.rot_unpack(10, 4, P, None, 10, None) == 1    # no A
+    assert lib.rot_pack(0, 4, None, 1, None, None) == 0     # nothing to do
+    assert lib.rot_apply_packed(10, 4, 2, None, P, 3, P, 3, None) == 1
+    assert lib.rot_apply_packed(10, 4, 2, P, P, 2, P, 3, None) == 1   # ldc < n-1
+    assert lib.rot_apply_packed(10, 1, 2, None, None, 1, None, 1, None) == 0
+    assert lib.rot_apply_packed_f32(-1, 4, 2, P, P, 3, P, 3, None) == 1
+    assert lib.rot_apply_packed_f32(10, 4, 0, None, None, 3, None, 3, None) == 0

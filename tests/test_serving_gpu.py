@@ -137,8 +137,8 @@ def test_destroy_drains_submitted_work(api):
 
 
 def test_wide_and_narrow_matrices_mixed_equal_sequential_oracle(api):
-    """Matrices of 1024 rows or more go out in launches of their own (one at a
-    time, one CTA per SM); small ones in other launches beside them.  Every
+    """Matrices of wide_rows rows or more go out in launches of their own (one
+    at a time, one CTA per SM); small ones in other launches beside them.  Every
     matrix still ends equal to the oracle's sequential application, and each
     request reports a latency."""
     r = np.random.default_rng(17)
@@ -151,7 +151,7 @@ def test_wide_and_narrow_matrices_mixed_equal_sequential_oracle(api):
         i = int(r.integers(0, len(shapes)))
         k = int(r.integers(2, 40))
         reqs.append((i,) + wl.rotations(shapes[i][1], k, seed=9500 + q))
-    with api.Server(hbm_budget_bytes=512 << 20, max_inflight=16, streams=4, max_batch=6) as srv:
+    with api.Server(hbm_budget_bytes=512 << 20, max_inflight=16, streams=4, max_batch=6, wide_rows=1024) as srv:
         handles = [srv.register(A) for A in devm]
         tickets = [srv.submit(handles[i], C, S) for (i, C, S) in reqs]
         lat = [srv.wait_latency(t, 60000) for t in tickets]
