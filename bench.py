@@ -382,7 +382,7 @@ def main():
     # registers only, at the wave kernel's launch shape (2 CTAs x 8 warps per SM)
     # and at full occupancy: the best of these is the measured rotation ceiling.
     mix = {}
-    for kind in ("rotation", "rotation_smem", "dfma", "dmul"):
+    for kind in ("rotation", "rotation_smem", "rotation_fma_smem", "dfma", "dmul", "dfma_smem"):
         for wpc, cps in ((8, 2), (32, 2)):
             r, _ = api.measure_fp64_mix(kind, wpc, cps)
             mix["%s_%dw" % (kind, wpc * cps)] = r

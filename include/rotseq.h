@@ -531,7 +531,12 @@ rot_status rot_measure_fp64_peak(double* gflops, double* ms);
  *   kind 2  the rotation's mix: per pair sy = RN(s*y), sx = RN(s*x),
  *           x' = fma(c,x,sy), y' = fma(c,y,-sx)
  *   kind 3  kind 2 with (c, s) read from shared memory per rotation
- * Every thread updates 4 independent pairs per iteration; the grid is
+ *   kind 4  kind 3 with the products as fma(s, y, -0), fma(s, x, -0) (a
+ *           freshly computed -0; bit-identical to the rounded products):
+ *           the form the library's FP64 rotation kernels use
+ *   kind 5  DFMA only, multiplier and addend read from shared memory
+ * Every thread updates 4 independent pairs per iteration (kind 4 counts 4
+ * FP64 instructions per pair and iteration, kind 5 two); the grid is
  * ctas_per_sm CTAs of warps_per_cta warps per SM (warps_per_cta 1..32,
  * ctas_per_sm 1..32, their product <= 64).  *lane_ops_per_s counts FP64
  * instructions times the lanes that executed them, per second (a rotation

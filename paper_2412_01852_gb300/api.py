@@ -179,7 +179,8 @@ def measure_fp64_peak():
     return g.value, ms.value
 
 
-FP64_MIX_KINDS = {"dfma": 0, "dmul": 1, "rotation": 2, "rotation_smem": 3}
+FP64_MIX_KINDS = {"dfma": 0, "dmul": 1, "rotation": 2, "rotation_smem": 3, "rotation_fma_smem": 4,
+                  "dfma_smem": 5}
 
 
 def measure_fp64_mix(kind, warps_per_cta, ctas_per_sm):

@@ -123,8 +123,12 @@ struct PipeState {
   T last[R];                           // the lane's last stage's output
 };
 
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+// RN(a*b): FMUL in FP32; in FP64 a DFMA with a freshly computed -0 addend
+// (bit-identical, and issued faster than DMUL on GB300; see mul_as_fma).
+__device__ __forceinline__ float mul_rn(float a, float b, float) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b, double nz) { return mul_as_fma(a, b, nz); }
+__device__ __forceinline__ float neg_zero_for(float) { return -0.0f; }
+__device__ __forceinline__ double neg_zero_for(double s) { return neg_zero_from(s); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
@@ -133,12 +137,13 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 // through unchanged.
 template <typename T, int R, bool FAST>
 __device__ __forceinline__ void pipe_stage(T (&carry)[R], const T (&y)[R], T (&out)[R], T c, T sn, bool on) {
+  const T nz = neg_zero_for(sn);
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const T x = carry[i];
     if (FAST || on) {
-      out[i] = fma_rn(c, x, mul_rn(sn, y[i]));
-      carry[i] = fma_rn(c, y[i], -mul_rn(sn, x));
+      out[i] = fma_rn(c, x, mul_rn(sn, y[i], nz));
+      carry[i] = fma_rn(c, y[i], -mul_rn(sn, x, nz));
     } else {
       out[i] = x;
       carry[i] = y[i];

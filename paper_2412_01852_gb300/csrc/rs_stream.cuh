@@ -71,7 +71,8 @@ __device__ __forceinline__ void stream_tile(T (&win)[R][KR + 1], const T* at, co
       if (FULL || (l < k && j >= 0 && j <= n - 2)) {   // the same in every lane
         const V2 p = cs[i * KP + l];
 #pragma unroll
-        for (int r = 0; r < R; ++r) rotate(win[r][((i - 1 - l) % U + U) % U], win[r][((i - l) % U + U) % U], p.x, p.y);
+        for (int r = 0; r < R; ++r)
+          rotate_dmul(win[r][((i - 1 - l) % U + U) % U], win[r][((i - l) % U + U) % U], p.x, p.y);
       }
     }
     const int q = w + 1 - KR;                    // final: its last rotation was at wave q + k - 1

@@ -7,6 +7,7 @@
 #include <vector>
 #include <cuda_runtime.h>
 #include "rs_internal.h"
+#include "rs_wave.cuh"
 
 namespace rs {
 
@@ -88,6 +89,9 @@ __global__ void dfma_probe_kernel(double* out, double b, double c, int iters) {
 //   KIND 2: a rotation    2 DMUL + 2 DFMA with the wave kernel's placement
 //   KIND 3: a rotation whose (c, s) pair comes from shared memory (one
 //           broadcast 16-byte load per rotation, as in the wave kernel)
+//   KIND 4: KIND 3 with the two products as DFMAs with a freshly computed -0
+//           addend (the form the FP64 kernels use)
+//   KIND 5: two DFMA per pair, multiplier and addend from shared memory
 // Values stay bounded: |c| < 1 and the rotation is orthogonal.  c and s pass
 // through an opaque move so that they sit in registers (an FP64 instruction
 // that reads a kernel parameter straight from the constant bank issues more
@@ -98,7 +102,7 @@ __global__ void fp64_mix_probe_kernel(double* out, double c_arg, double s_arg, i
   asm volatile("mov.b64 %0, %1;" : "=d"(c) : "d"(c_arg));
   asm volatile("mov.b64 %0, %1;" : "=d"(s) : "d"(s_arg));
   __shared__ double2 tab[64];
-  if (KIND == 3) {
+  if (KIND >= 3) {
     for (int i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = make_double2(c, s * (1.0 - 1e-9 * i));
     __syncthreads();
   }
@@ -123,13 +127,20 @@ __global__ void fp64_mix_probe_kernel(double* out, double c_arg, double s_arg, i
         const double xn = __fma_rn(c, x[i], sy);
         y[i] = __fma_rn(c, y[i], -sx);
         x[i] = xn;
-      } else {
+      } else if constexpr (KIND == 3) {
         const double2 cs = tab[(it * NP + i) & 63];
         const double sy = __dmul_rn(cs.y, y[i]);
         const double sx = __dmul_rn(cs.y, x[i]);
         const double xn = __fma_rn(cs.x, x[i], sy);
         y[i] = __fma_rn(cs.x, y[i], -sx);
         x[i] = xn;
+      } else if constexpr (KIND == 4) {
+        const double2 cs = tab[(it * NP + i) & 63];
+        rotate(x[i], y[i], cs.x, cs.y);
+      } else {
+        const double2 cs = tab[(it * NP + i) & 63];
+        x[i] = __fma_rn(x[i], cs.x, cs.y);
+        y[i] = __fma_rn(y[i], cs.x, cs.y);
       }
     }
   }
@@ -218,7 +229,7 @@ rot_status rot_measure_fp64_peak(double* gflops, double* ms_out) {
 
 rot_status rot_measure_fp64_mix(int kind, int warps_per_cta, int ctas_per_sm, double* lane_ops_per_s,
                                 double* ms_out) {
-  if (!lane_ops_per_s || kind < 0 || kind > 3 || warps_per_cta < 1 || warps_per_cta > 32 ||
+  if (!lane_ops_per_s || kind < 0 || kind > 5 || warps_per_cta < 1 || warps_per_cta > 32 ||
       ctas_per_sm < 1 || ctas_per_sm > 32 || warps_per_cta * ctas_per_sm > 64)
     return ROT_EINVAL;
   int dev = 0, nsm = 0;
@@ -230,12 +241,13 @@ rot_status rot_measure_fp64_mix(int kind, int warps_per_cta, int ctas_per_sm, do
   const int threads = warps_per_cta * 32;
   const int blocks = nsm * ctas_per_sm;
   // About 16 ms per launch at 2 FP64 lanes per clock per SM and 2 GHz.
-  const double lanes_per_iter = (double)NP * (kind >= 2 ? 4 : 2);
+  const double lanes_per_iter = (double)NP * ((kind >= 2 && kind <= 4) ? 4 : 2);
   int iters = (int)(2.0e9 * 0.016 * 2.0 / (warps_per_cta * ctas_per_sm * 32.0 * lanes_per_iter));
   if (iters < 16) iters = 16;
   using K = void (*)(double*, double, double, int);
-  const K kernels[4] = {rs::fp64_mix_probe_kernel<0, NP>, rs::fp64_mix_probe_kernel<1, NP>,
-                        rs::fp64_mix_probe_kernel<2, NP>, rs::fp64_mix_probe_kernel<3, NP>};
+  const K kernels[6] = {rs::fp64_mix_probe_kernel<0, NP>, rs::fp64_mix_probe_kernel<1, NP>,
+                        rs::fp64_mix_probe_kernel<2, NP>, rs::fp64_mix_probe_kernel<3, NP>,
+                        rs::fp64_mix_probe_kernel<4, NP>, rs::fp64_mix_probe_kernel<5, NP>};
   double* buf = nullptr;
   e = cudaMalloc(&buf, sizeof(double) * blocks * threads);
   if (e != cudaSuccess) {

@@ -37,9 +37,45 @@ template <typename T> struct Pair;
 template <> struct Pair<double> { using type = double2; };
 template <> struct Pair<float> { using type = float2; };
 
+// -0.0, computed afresh from s by two integer operations (opaque to the
+// compiler, so it is neither folded into a constant nor hoisted).
+__device__ __forceinline__ double neg_zero_from(double s) {
+  unsigned long long r;
+  asm volatile("{\n\tand.b64 %0, %1, 0x8000000000000000;\n\tor.b64 %0, %0, 0x8000000000000000;\n\t}"
+               : "=l"(r)
+               : "l"((unsigned long long)__double_as_longlong(s)));
+  return __longlong_as_double((long long)r);
+}
+
+// RN(a*b) as a fused multiply-add with a -0 addend.  Bit-identical to the
+// rounded product for every input: the exact product v is rounded once in
+// both, v + (-0) = v for v != 0, and +0 + (-0) = +0, -0 + (-0) = -0 under
+// round-to-nearest; infinities, NaN, overflow and subnormal results come out
+// the same.  On GB300 the FP64 pipe issues DFMA faster than DMUL: measured on
+// the rotation's own mix (registers only, (c, s) from shared memory), 2 DMUL
+// + 2 DFMA reach 0.91 of the nominal pipe rate, 4 DFMA 0.95-0.99, but only
+// when the -0 comes from a freshly computed register (a loop-invariant
+// register operand, or a constant, issues at the DMUL rate).
+__device__ __forceinline__ double mul_as_fma(double a, double b, double neg_zero) {
+  return __fma_rn(a, b, neg_zero);
+}
+
 // Algorithm 1 with the fixed FMA placement:
-//   x' = fma(c, x, RN(s*y)),  y' = fma(c, y, -RN(s*x)).
+//   x' = fma(c, x, RN(s*y)),  y' = fma(c, y, -RN(s*x)),
+// the two rounded products taken as fma(s, ., -0) (see mul_as_fma).
 __device__ __forceinline__ void rotate(double& x, double& y, double c, double s) {
+  const double nz = neg_zero_from(s);
+  const double sy = mul_as_fma(s, y, nz);
+  const double sx = mul_as_fma(s, x, nz);
+  const double xn = __fma_rn(c, x, sy);
+  y = __fma_rn(c, y, -sx);
+  x = xn;
+}
+// The rotation with DMUL products (bit-identical to rotate).  For kernels
+// bound by the latency of one row's chain of rotations rather than by the
+// FP64 pipe's issue rate (the column stream at one or two sequences), where
+// the DFMA form measured slower (8192 x 8192, k = 1: 1.36 ms against 1.25).
+__device__ __forceinline__ void rotate_dmul(double& x, double& y, double c, double s) {
   const double sy = __dmul_rn(s, y);
   const double sx = __dmul_rn(s, x);
   const double xn = __fma_rn(c, x, sy);
@@ -53,6 +89,7 @@ __device__ __forceinline__ void rotate(float& x, float& y, float c, float s) {
   y = __fmaf_rn(c, y, -sx);
   x = xn;
 }
+__device__ __forceinline__ void rotate_dmul(float& x, float& y, float c, float s) { rotate(x, y, c, s); }
 
 // RN(a*b) computed on the integer pipe, bit-identical to DMUL (IEEE round to
 // nearest even) whenever a and b are normal and the product is a normal
@@ -134,10 +171,19 @@ __device__ __forceinline__ void rotate_intmul(double& x, double& y, double c, do
 // A 2x2 reflector H = I - tau*v*v^T, v = (1, nu), applied to the row pair
 // (Section 6: three multiplications and three additions), with the fixed
 // placement t = fma(nu, y, x), w = RN(tau*t), x' = RN(x - w), y' = fma(-nu, w, y).
+// In FP64 the product and the difference are DFMAs with freshly computed
+// constants: RN(tau*t) = fma(tau, t, -0) and RN(x - w) = fma(w, -1, x), both
+// bit-identical (the product by -1 is exact), issued at the DFMA rate.
 __device__ __forceinline__ void reflect(double& x, double& y, double tau, double nu) {
+  const double nz = neg_zero_from(tau);
+  unsigned long long m1b;
+  asm volatile("{\n\tand.b64 %0, %1, 0;\n\tor.b64 %0, %0, 0xBFF0000000000000;\n\t}"
+               : "=l"(m1b)
+               : "l"((unsigned long long)__double_as_longlong(nu)));
+  const double m1 = __longlong_as_double((long long)m1b);   // -1.0
   const double t = __fma_rn(nu, y, x);
-  const double w = __dmul_rn(tau, t);
-  const double xn = __dsub_rn(x, w);
+  const double w = mul_as_fma(tau, t, nz);
+  const double xn = __fma_rn(w, m1, x);
   y = __fma_rn(-nu, w, y);
   x = xn;
 }

@@ -164,7 +164,7 @@ def test_device_codes_map_to_distinct_statuses(lib):
 
 def test_fp64_mix_probe_argument_checks_without_device(lib):
     d = ctypes.c_double(0)
-    for args in [(-1, 8, 1), (4, 8, 1), (0, 0, 1), (0, 33, 1), (0, 8, 0), (0, 32, 3)]:
+    for args in [(-1, 8, 1), (6, 8, 1), (0, 0, 1), (0, 33, 1), (0, 8, 0), (0, 32, 3)]:
         assert lib.rot_measure_fp64_mix(*args, ctypes.byref(d), None) == 1, args
     assert lib.rot_measure_fp64_mix(0, 8, 2, None, None) == 1
 
