@@ -46,11 +46,11 @@ UNIT = "rot-rows/s"
 # summarised in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum),
 # together with a hash of the kernel sources it was taken on.  If the kernel
 # sources change, the number no longer applies and traffic is reported as null.
-# Captured on plain-8192x4096 (0.5103e9 B per launch) and scaled by the
+# Captured on plain-8192x4096 (0.5084e9 B per launch) and scaled by the
 # rotation-rows of plain-8192 (x2.00024): consecutive p-blocks follow each other
 # closely enough that A's columns are still in L2 for the next p-block, so the
 # kernel reads and writes A about once and its traffic grows with n.
-NCU_TRAFFIC = {"bytes": 1.0207e9, "kernel_src_sha": "89379a2d22527eb6"}
+NCU_TRAFFIC = {"bytes": 1.0170e9, "kernel_src_sha": "0d949a02ccb03b30"}
 
 # The same for the single-p-block column stream at k = 1 (FP32, 8192 x 8192),
 # captured on the full workload (the kernel takes 0.1 ms).
@@ -480,9 +480,11 @@ def main():
                          "fp64_pipe_lanes_per_s_probes": mix,
                          "rotation_probe_tflops": rot_probe_tflops,
                          "frac_of_rotation_probe": achieved_tflops / rot_probe_tflops,
-                         "rotation_probe": "best FP64 rate of the rotation's own instruction mix (2 DMUL + 2 "
-                                           "DFMA per rotation-row), registers only, (c,s) in registers or read "
-                                           "from shared memory, 16 or 64 warps per SM; 6 flops per 4 lane-ops"},
+                         "rotation_probe": "best FP64 rate of the rotation's own instruction mix (4 FP64 "
+                                           "instructions per rotation-row: the products as DMUL or as DFMA with "
+                                           "a -0 addend, bit-identical), registers only, (c,s) in registers or "
+                                           "read from shared memory, 16 or 64 warps per SM; 6 flops per 4 "
+                                           "lane-ops"},
             "cpu_baseline": cpu,
             "cpu_parallel": cpu_par,
             "e2e": e2e,

@@ -310,7 +310,8 @@ typedef struct {
   int NB;            /* waves per work item, rounded up to a multiple of 16 (default 32) */
   int ctas_per_sm;   /* resident CTAs of 8 warps per SM (default: occupancy limit) */
   int fp64_products; /* where the FP64 rotation's two products run: 0 default
-                        (= 1), 1 FP64 pipe (DMUL), 2 integer pipe (bit-identical
+                        (= 1), 1 FP64 pipe (as fma(s, x, -0), bit-identical to
+                        DMUL and issued faster), 2 integer pipe (bit-identical
                         emulation, DMUL only for zero, subnormal, Inf/NaN or
                         out-of-range operands; slower on GB300); the FP32 path
                         ignores it */
