@@ -123,8 +123,10 @@ struct PipeState {
   T last[R];                           // the lane's last stage's output
 };
 
-// RN(a*b): FMUL in FP32; in FP64 a DFMA with a freshly computed -0 addend
-// (bit-identical, and issued faster than DMUL on GB300; see mul_as_fma).
+// RN(a*b): FMUL in FP32 (an FFMA with a freshly computed -0 addend measured
+// no faster there: 2.744 ms against 2.733 at 8192 x 8192, k = 192); in FP64 a
+// DFMA with a freshly computed -0 addend (bit-identical, and issued faster
+// than DMUL on GB300; see mul_as_fma).
 __device__ __forceinline__ float mul_rn(float a, float b, float) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b, double nz) { return mul_as_fma(a, b, nz); }
 __device__ __forceinline__ float neg_zero_for(float) { return -0.0f; }
