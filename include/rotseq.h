@@ -527,7 +527,7 @@ rot_status rot_measure_fp64_peak(double* gflops, double* ms);
 
 /* FP64 issue rate of one instruction mix, registers only, as a ceiling for
  * the rotation kernels (the paper counts 6 flops per rotation-row; with the
- * placement above that is 2 DMUL + 2 DFMA, Section 1.1):
+ * placement above that is two rounded products and two FMAs, Section 1.1):
  *   kind 0  DFMA only      kind 1  DMUL only
  *   kind 2  the rotation's mix: per pair sy = RN(s*y), sx = RN(s*x),
  *           x' = fma(c,x,sy), y' = fma(c,y,-sx)
