@@ -386,7 +386,7 @@ rot_status rot_apply_batched_ws(int count, const rot_problem* problems, void* wo
                                 void* stream);
 
 /*
- * Autotuner: times a small grid of tilings (K in {8,16}, NB in {32,64,128},
+ * Autotuner: times a small grid of tilings (K in {4,8,16}, NB in {32,64,128},
  * CTAs per SM in {1,2}) on scratch copies of the problems' A (so the caller's
  * data is not modified), stores the fastest in an in-process cache keyed by
  * the batch's shape signature and the device (and appends it to the file
@@ -396,6 +396,11 @@ rot_status rot_apply_batched_ws(int count, const rot_problem* problems, void* wo
  */
 rot_status rot_batch_autotune(int count, const rot_problem* problems, void* stream,
                               rot_tuning* best, float* best_ms);
+/* A batch of one problem tunes that shape for rot_apply too: when rot_apply
+ * (or rot_apply_left, on the transpose) takes the wavefront kernel (k > 32,
+ * or where the faster small-k kernels do not apply), it uses the tiling the
+ * cache holds for its shape signature, else the defaults.  The result is the
+ * same for every tiling. */
 
 /* ---- serving: continuous batching of requests on resident matrices ------ */
 

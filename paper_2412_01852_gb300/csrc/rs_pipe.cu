@@ -545,7 +545,17 @@ rot_status apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, co
                      const double* S, int64_t lds, cudaStream_t s) {
   if (pipe_f64_fits(m, n, k)) return pipe_apply_f64(m, n, k, A, lda, C, ldc, S, lds, s);
   if (stream_fits<double>(m, n, k, A, lda)) return stream_apply<double>(m, n, k, A, lda, C, ldc, S, lds, s);
-  return wave_apply<double>(m, n, k, A, lda, C, ldc, S, lds, s, WaveOptions{});
+  // The tiling the autotuner recorded for this shape (rot_batch_autotune on
+  // a batch of this one problem), else the defaults.
+  rot_problem p{m, n, k, A, lda, C, ldc, S, lds};
+  rot_tuning tu{};
+  tuning_lookup(1, &p, &tu);
+  WaveOptions o{};
+  o.K = tu.K;
+  o.NB = tu.NB;
+  o.ctas_per_sm = tu.ctas_per_sm;
+  o.fp64_products = tu.fp64_products;
+  return wave_apply<double>(m, n, k, A, lda, C, ldc, S, lds, s, o);
 }
 
 bool pipe_f64_fits(int64_t m, int64_t n, int64_t k) {

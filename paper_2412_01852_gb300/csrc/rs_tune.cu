@@ -104,7 +104,7 @@ extern "C" rot_status rot_batch_autotune(int count, const rot_problem* problems,
     if (cudaMemcpyAsync(d, q.A, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) st = ROT_ECUDA;
     q.A = static_cast<double*>(d);
   }
-  const int Ks[] = {8, 16};
+  const int Ks[] = {4, 8, 16};
   const int NBs[] = {32, 64, 128};
   const int Cs[] = {1, 2};
   float best_t = -1.f;
