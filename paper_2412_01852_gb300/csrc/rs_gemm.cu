@@ -511,26 +511,32 @@ struct FormLayout {
 
 // Rotation-row updates that run_item executes for one formation instance
 // (rows < m only): the same wave and rotation bounds as the kernel, including
-// the waves it skips because a chain's rows are still zero there.
+// the waves it skips because a chain's rows are still zero there.  Per
+// p-block the rotations of every wave are summed once (a prefix sum over the
+// waves); each chain then takes the sum over its waves.
 static long long executed_rotation_rows(const WaveInstance& I) {
   long long total = 0;
-  for (int c = 0; c < I.nchains; ++c) {
-    const int rows = std::min(32, I.m - 32 * c);
-    long long per_row = 0;
-    for (int g = 0; g < I.G; ++g) {
-      const int p0 = g * I.K;
-      const int kr = std::min(I.K, I.k - p0);
-      const int nw = I.n + kr - 2;
-      int wr_lo = I.W_lo - p0;
-      const int wr_hi = I.W_hi - p0;
-      if (I.unit_rows) wr_lo = std::max(wr_lo, c * 32 - p0 - 2);
-      for (int w = std::max(0, wr_lo); w < std::min(nw, wr_hi); ++w) {
-        const int l_lo = std::max(0, w - I.j_hi);
-        const int l_hi = std::min(kr - 1, w - I.j_lo);
-        if (l_hi >= l_lo) per_row += l_hi - l_lo + 1;
-      }
+  std::vector<long long> prefix;
+  for (int g = 0; g < I.G; ++g) {
+    const int p0 = g * I.K;
+    const int kr = std::min(I.K, I.k - p0);
+    const int nw = I.n + kr - 2;
+    const int wr_hi = std::min(nw, I.W_hi - p0);
+    const int w_lo = std::max(0, I.W_lo - p0);
+    // prefix[w] = rotations in waves [w_lo, w) of this p-block
+    prefix.assign((size_t)std::max(0, wr_hi - w_lo) + 1, 0);
+    for (int w = w_lo; w < wr_hi; ++w) {
+      const int l_lo = std::max(0, w - I.j_hi);
+      const int l_hi = std::min(kr - 1, w - I.j_lo);
+      prefix[(size_t)(w - w_lo) + 1] = prefix[(size_t)(w - w_lo)] + (l_hi >= l_lo ? l_hi - l_lo + 1 : 0);
     }
-    total += per_row * rows;
+    for (int c = 0; c < I.nchains; ++c) {
+      const int rows = std::min(32, I.m - 32 * c);
+      int lo = w_lo;
+      if (I.unit_rows) lo = std::max(lo, c * 32 - p0 - 2);
+      if (lo >= wr_hi) continue;
+      total += (prefix[(size_t)(wr_hi - w_lo)] - prefix[(size_t)(lo - w_lo)]) * rows;
+    }
   }
   return total;
 }
