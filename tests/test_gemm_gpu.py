@@ -109,7 +109,11 @@ def test_form_blocks_f32_rejects_kb_over_128(api):
 @pytest.mark.parametrize("mode", ["dmma", "f16", "bf16", "f16-q32", "bf16-q32"])
 @pytest.mark.parametrize("m,n,k,nb,kb", [(100, 300, 40, 64, 16), (33, 130, 70, 32, 32),
                                          (257, 500, 64, 256, 64), (64, 40, 100, 16, 16),
-                                         (90, 200, 50, 16, 48)])
+                                         (90, 200, 50, 16, 48),
+                                         # 320-wide windows with few carried columns (two
+                                         # tensor-memory windows do not fit beside four Q
+                                         # stages, so the split modes take mma.sync)
+                                         (200, 700, 40, 288, 32), (150, 900, 30, 304, 16)])
 def test_apply_gemm_within_bound(api, mode, m, n, k, nb, kb):
     A, C, S = wl.problem(m, n, k, seed=m + n + k)
     ref = oracle.rot_sequence(A, C, S)
