@@ -4,7 +4,9 @@
 // applies sequence p entirely before p+1, so the passes compute the same
 // thing).  Measured at 8192 x 8192: a pass of 8 sequences takes 0.30 ms in
 // FP32 and 8.9 ms in FP64, where the wavefront kernel takes 2.0-2.3 ms
-// (FP32, k = 16..64) and 21.7 ms (FP64, k = 16) or 24.4 ms (k = 32).
+// (FP32, k = 16..64) and 21.7 ms (FP64, k = 16) or 24.4 ms (k = 32).  FP64
+// passes of one or two sequences on column-major A take the two-warp split
+// of the stream (stream_split_kernel).
 #include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -56,10 +58,26 @@ rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, con
       st = ROT_ECUDA;
       break;
     }
+    const int tr = trace_begin(kF64 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32, m * (n - 1) * k, s);
+    if constexpr (kF64 && KR <= 2) {
+      if (!packed && k == KR) {
+        // One or two FP64 sequences: each column's instructions split over two warps.
+        auto kfn = stream_split_kernel<KR>;
+        e = smem_opt_in(reinterpret_cast<const void*>(kfn), SplitShape<KR>::kSmem);
+        if (e != cudaSuccess) { st = cuda_failed(e, "stream: shared-memory opt-in"); break; }
+        kfn<<<(unsigned)((m + 31) / 32), 64, SplitShape<KR>::kSmem, s>>>(amap, csmap, A, lda, (int)m, (int)n,
+                                                                         status);
+        trace_end(tr, s);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { st = cuda_failed(e, "stream: kernel launch"); break; }
+        record_status_async(status, s);
+        count_launches(3);
+        break;
+      }
+    }
     auto kfn = stream_kernel<T, KR, R>;
     e = smem_opt_in(reinterpret_cast<const void*>(kfn), SS::kSmem);
     if (e != cudaSuccess) { st = cuda_failed(e, "stream: shared-memory opt-in"); break; }
-    const int tr = trace_begin(kF64 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32, m * (n - 1) * k, s);
     kfn<<<(unsigned)((m + 32 * R - 1) / (32 * R)), 32, SS::kSmem, s>>>(amap, csmap, A, packed ? 32 : lda, (int)m,
                                                                        (int)n, (int)k, status,
                                                                        packed ? (int)n : 0);

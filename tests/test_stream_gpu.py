@@ -102,3 +102,46 @@ def test_stream_8192_k1_sampled_rows(rs):
     idx = torch.from_numpy(rows).cuda()
     assert np.array_equal(bits(Ad[idx].cpu().numpy()), bits(ref))
     assert np.array_equal(bits(A32[idx].cpu().numpy()), bits(ref32))
+
+
+# FP64 passes of one or two sequences on column-major A run as two warps per
+# 32-row strip (one carrying the chain or the first sequence, the other the
+# finished columns or the second sequence), handing values over through a
+# ring of shared-memory tiles.  Ragged strips, padded leading dimensions, n
+# around the 20- and 21-column tiles and the ring's wrap (more than four
+# tiles), ±0 and infinities, bit-exact against the oracle.
+SPLIT_CASES = [(64, 64, 1, 0), (64, 64, 2, 0), (65, 81, 1, 2), (95, 80, 2, 4), (128, 126, 2, 0),
+               (200, 300, 1, 6), (333, 301, 2, 2), (1000, 1001, 2, 0), (97, 127, 1, 0), (160, 64, 2, 8)]
+
+
+@pytest.mark.parametrize("m,n,k,slack", SPLIT_CASES)
+def test_stream_split_f64_bit_exact(rs, m, n, k, slack):
+    A, C, S = wl.problem(m, n, k, seed=7 * m + n + k)
+    A[::7, ::5] = -0.0
+    A[3, 2] = np.inf
+    A[5, n - 1] = -np.inf
+    ref = oracle.rot_sequence(A, C, S)
+    Ad, buf = dev(A, (m + slack + 1) // 2 * 2)
+    rs.rot_apply(Ad, dev(C)[0], dev(S)[0])
+    rs.rot_device_status()
+    out = buf.cpu().numpy()
+    # Two infinities meeting in one rotation make NaNs (Inf - Inf); their bit
+    # patterns are platform-specific, their places are not.
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(out[:m, :n]), nan)
+    assert np.array_equal(bits(out[:m, :n][~nan]), bits(ref[~nan]))
+    assert np.all(np.isnan(out[m:, :n]))
+
+
+def test_stream_split_8192_k2_sampled_rows(rs):
+    m = n = 8192
+    A = wl.matrix(m, n, 2)
+    C, S = wl.rotations(n, 2, 2)
+    r = np.random.default_rng(81)
+    rows = np.unique(np.concatenate([[0, 31, 32, m - 1], r.choice(m, 28, replace=False)]))
+    ref = oracle.rot_sequence(A[rows], C, S)
+    Ad = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+    rs.rot_apply(Ad, dev(C)[0], dev(S)[0])
+    rs.rot_device_status()
+    idx = torch.from_numpy(rows).cuda()
+    assert np.array_equal(bits(Ad[idx].cpu().numpy()), bits(ref))
