@@ -158,186 +158,226 @@ stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
 }
 
 // ---------------------------------------------------------------------------
-// FP64, one or two sequences: the column stream split over two warps.
+// FP64, one or two sequences: the column stream split over warps.
 //
 // GB300's FP64 unit belongs to an SM sub-partition and takes 64 cycles for a
-// warp instruction, whatever its active lanes.  A row's chain of rotations is
-// sequential, so one warp streaming its 32 rows alone costs 4 instructions x
-// 64 cycles per column at k = 1 (8 at k = 2) however many warps run beside
-// it.  Two warps of one CTA, on different sub-partitions, share each column's
-// instructions; the arithmetic is rotate_dmul's, every element sees the same
-// operations on the same operands, so the result is bit-identical.
-//   k = 1: warp A carries the chain, x <- fma(c, y, -RN(s*x)) (2
-//          instructions a column), and hands each column's incoming x to
-//          warp B, which forms the finished column fma(c, x, RN(s*y)).
-//   k = 2: warp A applies sequence 0 (4 instructions a column) and hands its
-//          finished columns to warp B, which applies sequence 1 to them.
-// The hand-off is a ring of RING tiles of CB values per lane in shared
-// memory (ready/free barriers); the TMA stages are read by both warps and
-// refilled by warp B, their last reader, once warp A is done with them too.
-// Measured at n = 8192 (kernel time the same for 76 to 304 strips, so a
-// warp's own dependent chain is the bound): k = 1 1.20 ms, 302 cycles a
-// column, two dependent FP64 instructions of about 151 cycles each (one warp
-// alone: 1.26 ms); k = 2 1.83 ms (one warp: 2.32 ms).  The chain's product
-// on the integer pipe (dmul_int) was slower: 1.67 ms at k = 1.
+// warp instruction, whatever its active lanes, and a row's chain of
+// rotations is sequential: column after column, x <- fma(c, y, -RN(s*x)).
+// Issued in order, every other FP64 instruction of the warp (the finished
+// column fma(c, x, RN(s*y)) and its product) delays that chain.  So each warp
+// here carries only two FP64 instructions a column:
+//   k = 1: warp 0 the chain, handing each column's incoming x to warp 1,
+//          which forms the finished column;
+//   k = 2: warp 0 the chain of sequence 0, warp 1 its finished columns,
+//          warp 2 the chain of sequence 1 over those columns, warp 3 their
+//          finished columns (the result).
+// Every element sees rotate_dmul's operations on the same operands, in the
+// same order: bit-identical.  Values pass between warps through rings of
+// RING tiles of CB values per lane in shared memory (ready/free barriers);
+// the TMA stages are read by every warp and refilled by the last one, once
+// the others are done with them.
+// Each warp's role is a template parameter, so a chain warp's per-column path
+// holds nothing but its two FP64 instructions, their loads and the hand-off
+// store (with the roles as runtime branches: k = 1 1.33 ms).  Measured at
+// 8192 x 8192 (kernel time the same for 76 to 152 strips of 32 rows, so a
+// warp's own dependent chain is the bound): k = 1 1.13 ms, 280 cycles a
+// column (one warp per strip: 1.26 ms); k = 2 1.48 ms (one warp: 2.32 ms; two
+// warps, one per sequence: 1.83 ms).  The chain's product on the integer pipe
+// (dmul_int) was slower: 1.67 ms at k = 1 (two-warp build).
 template <int KR>
 struct SplitShape {
   using SS = StreamShape<double, KR, 1>;
-  static constexpr int RING = 4;
+  static constexpr int NW = 2 * KR;                        // warps
+  static constexpr int NRING = NW - 1;                     // rings between consecutive warps
+  static constexpr int RING = KR == 1 ? 4 : 2;             // tiles per ring
   static constexpr int kRingTile = SS::CB * 32 * (int)sizeof(double);
   static constexpr int kRingOff = SS::S * SS::kStage;
-  static constexpr int kBarOff = kRingOff + RING * kRingTile;
-  // barriers: full[S], consumed[S], ready[RING], ring_free[RING]; then the abort flag
-  static constexpr int kSmem = kBarOff + (2 * SS::S + 2 * RING) * 8 + 16;
+  static constexpr int kBarOff = kRingOff + NRING * RING * kRingTile;
+  // barriers: full[S], consumed[S], ready[NRING][RING], free[NRING][RING]; then the abort flag
+  static constexpr int kSmem = kBarOff + (2 * SS::S + 2 * NRING * RING) * 8 + 16;
 };
 
+// Shared state of one CTA of stream_split_kernel.
+struct SplitCta {
+  const CUtensorMap* amap;
+  const CUtensorMap* csmap;
+  unsigned char* smem;
+  uint64_t* full;
+  uint64_t* consumed;
+  uint64_t* ready;
+  uint64_t* freed;
+  volatile int* abort_flag;
+  double* A;
+  int64_t lda;
+  int m, n, c, lane, ntiles;
+  int* status;
+};
+
+// The tile loop of warp W (its role fixed at compile time, so that a chain
+// warp's per-column path holds nothing but its two FP64 instructions, the
+// loads feeding them and the hand-off store).
+template <int KR, int W>
+__device__ __forceinline__ void split_role(const SplitCta& X) {
+  using SS = StreamShape<double, KR, 1>;
+  using SP = SplitShape<KR>;
+  using V2 = typename Pair<double>::type;
+  constexpr int CB = SS::CB, S = SS::S, KP = SS::KP, RING = SP::RING, NW = SP::NW;
+  constexpr bool kChain = (W & 1) == 0;         // a chain (else finished columns)
+  constexpr int kSeq = W / 2;                   // its sequence
+  constexpr bool kWrites = W < NW - 1;          // hands values to the next warp
+  constexpr bool kReadsPrev = W > 0;
+  constexpr bool kReadsR1 = KR == 2 && W == 3;  // sequence 1's input columns
+  constexpr bool kLast = W == NW - 1;
+  const int lane = X.lane, n = X.n;
+  auto ring = [&](int g, int q) {
+    return reinterpret_cast<double*>(X.smem + SP::kRingOff) + ((size_t)g * RING + q) * CB * 32 + lane;
+  };
+  auto wait = [&](uint64_t* bar, uint32_t parity) {
+    bool ok = !*X.abort_flag && mbar_wait_bounded(bar, parity);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && lane == 0) {
+      if (!*X.abort_flag) set_error(X.status, kDevTimeoutTma);
+      *X.abort_flag = 1;
+    }
+    return ok;
+  };
+  auto issue = [&](int t) {
+    const int s = t % S;
+    unsigned char* st = X.smem + s * SS::kStage;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&X.full[s], SS::kABytes + SS::kCsBytes);
+    tma_load_2d(st, X.amap, &X.full[s], X.c * 32, t * CB);
+    tma_load_2d(st + SS::kAStage, X.csmap, &X.full[s], 0, t * CB - 1);
+  };
+  const bool rowok = X.c * 32 + lane < X.m;
+  double x = 0.0;                               // a chain's carried value
+  double* ps = X.A + (int64_t)X.c * 32 + lane;  // the last warp's next column
+  int issued = X.ntiles < S ? X.ntiles : S;
+  int t = 0;
+  for (; t < X.ntiles; ++t) {
+    const int s = t % S, q = t % RING;
+    const uint32_t use = (uint32_t)(t / RING);
+    if (!wait(&X.full[s], (uint32_t)(t / S) & 1u)) break;
+    if (kReadsPrev && !wait(&X.ready[(W - 1) * RING + q], use & 1u)) break;
+    if (kReadsR1 && !wait(&X.ready[1 * RING + q], use & 1u)) break;
+    if (kWrites && t >= RING && !wait(&X.freed[W * RING + q], (use - 1) & 1u)) break;
+    const double* at = reinterpret_cast<const double*>(X.smem + s * SS::kStage) + lane;
+    const V2* cs = reinterpret_cast<const V2*>(X.smem + s * SS::kStage + SS::kAStage) + kSeq;
+    double* out = kWrites ? ring(W, q) : nullptr;
+    const double* in = kReadsPrev ? ring(W - 1, q) : nullptr;
+    const double* in1 = kReadsR1 ? ring(1, q) : nullptr;
+    // Sequence kSeq takes its input column j + 1 at wave w = j + kSeq; its
+    // rotation (j, j+1) has the pair of wave w, index kSeq.
+    const int j0 = t * CB - 1 - kSeq;
+#pragma unroll 4
+    for (int i = 0; i < CB; ++i) {
+      const int j = j0 + i;
+      if constexpr (kChain) {
+        const double y = kSeq == 0 ? at[i * 32] : in[i * 32];   // input column j + 1
+        if (j >= 0 && j <= n - 2) {
+          out[i * 32] = x;                      // column j's incoming value
+          x = __fma_rn(cs[i * KP].x, y, -__dmul_rn(cs[i * KP].y, x));
+        } else if (j == -1) {
+          x = y;                                // input column 0
+        } else if (j == n - 1) {
+          out[i * 32] = x;                      // the last column, final for this sequence
+        }
+      } else {
+        if (j >= 0 && j <= n - 1) {
+          double v = in[i * 32];                // column j's incoming value (final at j = n-1)
+          if (j <= n - 2) {
+            const double y = kSeq == 0 ? at[i * 32] : in1[i * 32];
+            v = __fma_rn(cs[i * KP].x, v, __dmul_rn(cs[i * KP].y, y));
+          }
+          if constexpr (kLast) {
+            if (rowok) st_cg(ps, v);            // column j, final
+            ps += X.lda;
+          } else {
+            out[i * 32] = v;                    // column j after sequence 0, for the next chain
+          }
+        }
+      }
+    }
+    if constexpr (kWrites) mbar_arrive(&X.ready[W * RING + q]);
+    if constexpr (kReadsPrev) mbar_arrive(&X.freed[(W - 1) * RING + q]);
+    if constexpr (kReadsR1) mbar_arrive(&X.freed[1 * RING + q]);
+    if constexpr (!kLast) {
+      mbar_arrive(&X.consumed[s]);
+    } else {
+      // The last reader of stage s: refill it with tile t + S once the
+      // other warps are done with it.
+      __syncwarp();
+      if (t + S < X.ntiles) {
+        if (!wait(&X.consumed[s], (uint32_t)(t / S) & 1u)) break;
+        if (lane == 0) issue(t + S);
+        ++issued;
+      }
+    }
+  }
+  // On a timeout, let the copies still in flight land before leaving.
+  if (kLast && t < X.ntiles && lane == 0)
+    for (int u = t + 1; u < issued; ++u) (void)mbar_wait_bounded(&X.full[u % S], (uint32_t)(u / S) & 1u);
+}
+
 template <int KR>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(64 * KR)
 stream_split_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap csmap, double* A,
                     int64_t lda, int m, int n, int* status) {
   static_assert(KR == 1 || KR == 2, "one or two sequences");
   using SS = StreamShape<double, KR, 1>;
   using SP = SplitShape<KR>;
-  using V2 = typename Pair<double>::type;
-  constexpr int CB = SS::CB, S = SS::S, KP = SS::KP, RING = SP::RING;
+  constexpr int CB = SS::CB, S = SS::S, RING = SP::RING, NW = SP::NW, NRING = SP::NRING;
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SP::kBarOff);
-  uint64_t* consumed = full + S;
-  uint64_t* ready = consumed + S;
-  uint64_t* ring_free = ready + RING;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(ring_free + RING);
-  double* ring = reinterpret_cast<double*>(smem + SP::kRingOff);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = blockIdx.x;                     // strip of 32 rows
-  const bool rowok = c * 32 + lane < m;
-  double* const arow = A + (int64_t)c * 32 + lane;
-  const int ntiles = (n + KR + CB - 1) / CB;    // waves -1 .. n-2+KR
-  auto issue = [&](int t) {
-    const int s = t % S;
-    unsigned char* st = smem + s * SS::kStage;
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&full[s], SS::kABytes + SS::kCsBytes);
-    tma_load_2d(st, &amap, &full[s], c * 32, t * CB);
-    tma_load_2d(st + SS::kAStage, &csmap, &full[s], 0, t * CB - 1);
-  };
+  SplitCta X;
+  X.amap = &amap;
+  X.csmap = &csmap;
+  X.smem = smem;
+  X.full = reinterpret_cast<uint64_t*>(smem + SP::kBarOff);
+  X.consumed = X.full + S;
+  X.ready = X.consumed + S;                     // ready[g * RING + q]: ring g, slot q written
+  X.freed = X.ready + NRING * RING;             // freed[g * RING + q]: ring g, slot q read by all its readers
+  X.abort_flag = reinterpret_cast<volatile int*>(X.freed + NRING * RING);
+  X.A = A;
+  X.lda = lda;
+  X.m = m;
+  X.n = n;
+  X.c = blockIdx.x;                             // strip of 32 rows
+  X.lane = threadIdx.x & 31;
+  X.ntiles = (n + KR + CB - 1) / CB;            // waves -1 .. n-2+KR
+  X.status = status;
   if (threadIdx.x == 0) {
     prefetch_tmap(&amap);
     prefetch_tmap(&csmap);
     for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&consumed[s], 32);
+      mbar_init(&X.full[s], 1);
+      mbar_init(&X.consumed[s], 32 * (NW - 1));   // every warp but the last
     }
-    for (int r = 0; r < RING; ++r) {
-      mbar_init(&ready[r], 32);
-      mbar_init(&ring_free[r], 32);
-    }
-    *abort_flag = 0;
+    for (int g = 0; g < NRING; ++g)
+      for (int q = 0; q < RING; ++q) {
+        mbar_init(&X.ready[g * RING + q], 32);
+        // ring 1 of k = 2 (sequence 0's finished columns) is read by warps 2 and 3
+        mbar_init(&X.freed[g * RING + q], (KR == 2 && g == 1) ? 64 : 32);
+      }
+    *X.abort_flag = 0;
     fence_mbarrier_init();
-    for (int t = 0; t < S && t < ntiles; ++t) issue(t);
+    for (int t = 0; t < S && t < X.ntiles; ++t) {
+      unsigned char* st = smem + t * SS::kStage;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&X.full[t], SS::kABytes + SS::kCsBytes);
+      tma_load_2d(st, &amap, &X.full[t], X.c * 32, t * CB);
+      tma_load_2d(st + SS::kAStage, &csmap, &X.full[t], 0, t * CB - 1);
+    }
   }
   __syncthreads();
-  // A bounded wait that also gives up once the other warp has.
-  auto wait = [&](uint64_t* bar, uint32_t parity) {
-    bool ok = !*abort_flag && mbar_wait_bounded(bar, parity);
-    ok = __all_sync(0xffffffffu, ok);
-    if (!ok && lane == 0) {
-      if (!*abort_flag) set_error(status, kDevTimeoutTma);
-      *abort_flag = 1;
-    }
-    return ok;
-  };
-  int issued = ntiles < S ? ntiles : S;         // tiles whose copies warp B has started (lane 0's count)
-  if (warp == 0) {
-    // ---- warp A: the upstream chain ------------------------------------------------
-    double x = 0.0;
-    for (int t = 0; t < ntiles; ++t) {
-      const int s = t % S, r = t % RING;
-      if (!wait(&full[s], (uint32_t)(t / S) & 1u)) break;
-      if (t >= RING && !wait(&ring_free[r], (uint32_t)(t / RING - 1) & 1u)) break;
-      const double* at = reinterpret_cast<const double*>(smem + s * SS::kStage);
-      const V2* cs = reinterpret_cast<const V2*>(smem + s * SS::kStage + SS::kAStage);
-      double* out = ring + (size_t)r * CB * 32 + lane;
-      const int w0 = t * CB - 1;
-#pragma unroll 4
-      for (int i = 0; i < CB; ++i) {
-        const int w = w0 + i;                   // wave w takes in column w + 1
-        const double y = at[i * 32 + lane];
-        if (w < 0) {
-          x = y;                                // column 0
-        } else if (w <= n - 2) {
-          const V2 p = cs[i * KP];              // rotation (w, w+1) of the first sequence
-          if constexpr (KR == 1) {
-            out[i * 32] = x;                    // the column's incoming value, for warp B
-            x = __fma_rn(p.x, y, -__dmul_rn(p.y, x));
-          } else {
-            const double sy = __dmul_rn(p.y, y);
-            const double sx = __dmul_rn(p.y, x);
-            out[i * 32] = __fma_rn(p.x, x, sy); // column w after the first sequence
-            x = __fma_rn(p.x, y, -sx);
-          }
-        } else if (w == n - 1) {
-          out[i * 32] = x;                      // the last column after the first sequence
-        }
-      }
-      mbar_arrive(&ready[r]);
-      mbar_arrive(&consumed[s]);
-    }
+  const int warp = threadIdx.x >> 5;
+  if constexpr (KR == 1) {
+    if (warp == 0) split_role<1, 0>(X);
+    else split_role<1, 1>(X);
   } else {
-    // ---- warp B: finished columns, stores, and the stage refills -----------------------
-    double x1 = 0.0;
-    double* ps = arow;                          // column 0 of this lane's row
-    int t = 0;
-    for (; t < ntiles; ++t) {
-      const int s = t % S, r = t % RING;
-      if (!wait(&full[s], (uint32_t)(t / S) & 1u)) break;
-      if (!wait(&ready[r], (uint32_t)(t / RING) & 1u)) break;
-      const double* at = reinterpret_cast<const double*>(smem + s * SS::kStage);
-      const V2* cs = reinterpret_cast<const V2*>(smem + s * SS::kStage + SS::kAStage);
-      const double* in = ring + (size_t)r * CB * 32 + lane;
-      const int w0 = t * CB - 1;
-#pragma unroll 4
-      for (int i = 0; i < CB; ++i) {
-        const int w = w0 + i;
-        if constexpr (KR == 1) {
-          if (w >= 0 && w <= n - 2) {
-            const V2 p = cs[i * KP];
-            const double v = __fma_rn(p.x, in[i * 32], __dmul_rn(p.y, at[i * 32 + lane]));
-            if (rowok) st_cg(ps, v);            // column w, final
-            ps += lda;
-          } else if (w == n - 1) {
-            if (rowok) st_cg(ps, in[i * 32]);   // column n-1, final
-            ps += lda;
-          }
-        } else {
-          if (w == 0) {
-            x1 = in[i * 32];                    // column 0 after the first sequence
-          } else if (w >= 1 && w <= n - 1) {
-            const V2 p = cs[i * KP + 1];        // rotation (w-1, w) of the second sequence
-            const double y1 = in[i * 32];
-            const double sy = __dmul_rn(p.y, y1);
-            const double sx = __dmul_rn(p.y, x1);
-            const double v = __fma_rn(p.x, x1, sy);
-            x1 = __fma_rn(p.x, y1, -sx);
-            if (rowok) st_cg(ps, v);            // column w-1, final
-            ps += lda;
-          } else if (w == n) {
-            if (rowok) st_cg(ps, x1);           // column n-1, final
-            ps += lda;
-          }
-        }
-      }
-      mbar_arrive(&ring_free[r]);
-      __syncwarp();
-      // Both warps are done with stage s: refill it with tile t + S.
-      if (t + S < ntiles) {
-        if (!wait(&consumed[s], (uint32_t)(t / S) & 1u)) break;
-        if (lane == 0) issue(t + S);
-        ++issued;
-      }
-    }
-    // On a timeout, let the copies still in flight land before leaving.
-    if (t < ntiles && lane == 0)
-      for (int u = t + 1; u < issued; ++u) (void)mbar_wait_bounded(&full[u % S], (uint32_t)(u / S) & 1u);
+    if (warp == 0) split_role<2, 0>(X);
+    else if (warp == 1) split_role<2, 1>(X);
+    else if (warp == 2) split_role<2, 2>(X);
+    else split_role<2, 3>(X);
   }
 }
 
