@@ -768,12 +768,15 @@ def variant_line(args):
             kern = [r[1] for r in recs if r[0] in (("wave_f32", "pipe_f32") if prec == "f32" else ("wave_f64", "pipe_f64"))]
             kms = sum(kern) / (3 + reps) if kern else ms       # every launch of a call (warm-up included)
             Wk = wl.rotation_rows(m, n, kk)
-            # FP32: the column stream makes one pass over A per 8 sequences (up to
-            # k = 48), the lane pipeline one per 192 (plus the k mod 32 left
-            # over).  FP64: one pass (the stream for k <= 2, the lane pipeline
-            # for 3 <= k <= 32, the wavefront kernel beyond).
+            # FP32: the column stream makes one pass over A per 8 sequences and
+            # one per binary digit of the rest (up to k = 48), the lane
+            # pipeline one per 192 (plus the k mod 32 left over, on the
+            # stream).  FP64: one pass (the stream for k <= 2, the lane
+            # pipeline for 3 <= k <= 32, the wavefront kernel beyond).
+            def stream_passes(r):
+                return r // 8 + bin(r % 8).count("1")
             if prec == "f32":
-                passes = -(-kk // 8) if kk <= 48 else -(-(kk // 32) // 6) + (-(-(kk % 32) // 8) if kk % 32 else 0)
+                passes = stream_passes(kk) if kk <= 48 else -(-(kk // 32) // 6) + stream_passes(kk % 32)
             else:
                 passes = 1
             nbytes = passes * 2 * m * n * esz + 2 * (n - 1) * kk * esz   # A read and written per pass, C and S read

@@ -61,12 +61,13 @@ rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, con
     const int tr = trace_begin(kF64 ? ROT_KERNEL_WAVE_F64 : ROT_KERNEL_WAVE_F32, m * (n - 1) * k, s);
     if constexpr (kF64 && KR <= 2) {
       if (!packed && k == KR) {
-        // One or two FP64 sequences: each column's instructions split over two warps.
+        // One or two FP64 sequences: each column's instructions split over
+        // two or four warps, two FP64 instructions a column each.
         auto kfn = stream_split_kernel<KR>;
         e = smem_opt_in(reinterpret_cast<const void*>(kfn), SplitShape<KR>::kSmem);
         if (e != cudaSuccess) { st = cuda_failed(e, "stream: shared-memory opt-in"); break; }
-        kfn<<<(unsigned)((m + 31) / 32), 64, SplitShape<KR>::kSmem, s>>>(amap, csmap, A, lda, (int)m, (int)n,
-                                                                         status);
+        kfn<<<(unsigned)((m + 31) / 32), 64 * KR, SplitShape<KR>::kSmem, s>>>(amap, csmap, A, lda, (int)m, (int)n,
+                                                                              status);
         trace_end(tr, s);
         e = cudaGetLastError();
         if (e != cudaSuccess) { st = cuda_failed(e, "stream: kernel launch"); break; }
@@ -106,16 +107,23 @@ bool stream_fits(int64_t m, int64_t n, int64_t k, const T* A, int64_t lda) {
 template <typename T>
 rot_status stream_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc, const T* S,
                         int64_t lds, cudaStream_t s, bool packed) {
-  for (int64_t p0 = 0; p0 < k; p0 += 8) {
-    const int64_t kk = std::min<int64_t>(8, k - p0);
+  // Passes of 8, 4, 2 or 1 sequences (8 while they last, then the binary
+  // digits of the rest), so that every pass fills its window: a window
+  // wider than its sequences runs every wave with predicates (FP32 at
+  // 8192 x 8192: k = 5 in one window of 8 took 1.41 ms, as 4 + 1 it takes
+  // about 0.28 ms; k = 3 in a window of 4 0.38 ms, as 2 + 1 about 0.23).
+  for (int64_t p0 = 0; p0 < k;) {
+    const int64_t left = k - p0;
+    const int64_t kk = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
     const T* Cp = C + p0 * ldc;
     const T* Sp = S + p0 * lds;
     rot_status st;
     if (kk == 1) st = stream_launch<T, 1>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s, packed);
     else if (kk == 2) st = stream_launch<T, 2>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s, packed);
-    else if (kk <= 4) st = stream_launch<T, 4>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s, packed);
+    else if (kk == 4) st = stream_launch<T, 4>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s, packed);
     else st = stream_launch<T, 8>(m, n, kk, A, lda, Cp, ldc, Sp, lds, s, packed);
     if (st != ROT_OK) return st;
+    p0 += kk;
   }
   return ROT_OK;
 }
