@@ -322,7 +322,7 @@ def main():
                     help="rows of the instance per reference step (0: all of them)")
     ap.add_argument("--variant", default="plain",
                     choices=["plain", "f32", "gemm-f16", "gemm-bf16", "gemm-dmma", "gemm-f16-q32",
-                             "gemm-bf16-q32", "batched", "serving", "reflectors", "left", "small-k"],
+                             "gemm-bf16-q32", "batched", "serving", "reflectors", "left", "small-k", "k-sweep"],
                     help="plain (default) is the measured line; the others measure the other "
                          "paths of the library on the same GPU")
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -717,6 +717,55 @@ def variant_line(args):
                                   "achieved": 6.0 * W / (kms * 1e-3) / 1e12, "peak": fp64_peak,
                                   "unit": "TFLOP/s"}})
         line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak
+        return line
+
+    if args.variant == "k-sweep":
+        # Whole calls of rot_apply (FP64) and rot_apply_f32 over k, on three
+        # shapes, to show how the dispatch (column stream, lane pipeline in
+        # passes or chunks, wavefront kernel) behaves between the fixed k of
+        # the other variants.  Median of four calls per k, each after an L2
+        # flush (a 256 MiB write), CUDA events around the call.
+        flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+
+        def call_ms(fn, reps=4):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return float(np.median(ts))
+
+        shapes = {}
+        for (m, n) in ((8192, 8192), (2048, 2048), (8192, 512)):
+            A = wl.matrix(m, n, 6)
+            per = {}
+            for prec in ("f32", "f64"):
+                Ad = _dev_colmajor(torch, A.astype(np.float32) if prec == "f32" else A, dev)
+                ks = list(range(1, 65)) if prec == "f32" else list(range(1, 41)) + [48, 64, 80, 96]
+                row = {}
+                for kk in ks:
+                    C, S = wl.rotations(n, kk, 6)
+                    if prec == "f32":
+                        Cd, Sd = (_dev_colmajor(torch, X.astype(np.float32), dev) for X in (C, S))
+                        fn = lambda: rs.rot_apply_f32(Ad, Cd, Sd)
+                    else:
+                        Cd, Sd = (_dev_colmajor(torch, X, dev) for X in (C, S))
+                        fn = lambda: rs.rot_apply(Ad, Cd, Sd)
+                    row[str(kk)] = call_ms(fn)
+                per[prec] = row
+            shapes["%dx%d" % (m, n)] = per
+        line.update({"value": None, "ms_per_step": None, "dtype": "f32/f64",
+                     "config": {"workload": "k sweep: A N(0,1) m x n column-major, uniform angles, seed 6",
+                                "shapes": list(shapes)},
+                     "ms_per_call": shapes})
         return line
 
     if args.variant == "small-k":

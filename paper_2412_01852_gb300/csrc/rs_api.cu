@@ -58,10 +58,15 @@ rot_status rot_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda,
   bool quick;
   rot_status v = validate(m, n, k, A, lda, C, ldc, S, lds, &quick);
   if (v != ROT_OK || quick) return v;
-  if (rs::stream_fits<float>(m, n, k, A, lda))
+  // The column stream up to 41 sequences, the lane pipeline beyond (where
+  // each applies; measured crossover at 8192 x 8192), the wavefront kernel
+  // otherwise.
+  if (k <= 41 && rs::stream_fits<float>(m, n, k, A, lda))
     return rs::stream_apply<float>(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream));
   if (rs::pipe_f32_fits(m, n, k))
     return rs::pipe_apply_f32(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream));
+  if (rs::stream_fits<float>(m, n, k, A, lda))
+    return rs::stream_apply<float>(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream));
   return rs::wave_apply_f32(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream),
                             rs::WaveOptions{});
 }

@@ -22,10 +22,11 @@
 // zeros keep their sign and infinities stay.
 //
 // FP32 (k >= 32): one group, up to 192 stages per pass, 7 rows, 4 warps per
-// CTA.  FP64 (3 <= k <= 32): GB300's FP64 unit takes as long for a warp
-// instruction whatever its active lanes, so every lane holds a stage: k is
-// rounded up to a power of two KS and the warp holds 32/KS independent
-// groups; CTAs of one warp up to KS = 16, of 4 warps at KS = 32.
+// CTA.  FP64 (3 <= k <= 32, and chunks of 32 up to k = 64): GB300's FP64
+// unit takes as long for a warp instruction whatever its active lanes, so
+// every lane holds a stage: k is rounded up to a power of two KS and the warp
+// holds 32/KS independent groups; CTAs of one warp up to KS = 16, of 4 warps
+// at KS = 32.
 //
 // The warps of a CTA run in step and share the (c,s) table through shared
 // memory: one bulk copy per 32-step tile, two or three tiles in flight,
@@ -42,6 +43,11 @@ namespace {
 
 constexpr int kPTC = 32;      // steps (columns) per tile
 constexpr int kPMaxSpl = 6;   // FP32 sequences per lane: 192 per pass
+// FP64 above 32 sequences: chunks of 32 on the lane pipeline up to here, the
+// wavefront kernel beyond (8192 x 8192: k = 33 16.4 ms against 24.7, k = 64
+// 30.5 against 32.3, k = 80 38.2 against 37.4; 2048 x 2048: k = 64 4.7
+// against 6.5, k = 96 6.9 against 7.0).
+constexpr int64_t kF64ChunkedMaxK = 64;
 
 // W: warps per CTA.
 template <typename T, int SPL, int G, int R, int W = 4>
@@ -486,24 +492,34 @@ rot_status pipe_table(int64_t n, int kp, int KS, const T* C, int64_t ldc, const 
 }  // namespace
 
 bool pipe_f32_fits(int64_t m, int64_t n, int64_t k) {
-  // Worth it where most tiles run without predicates: at least 32
-  // sequences, over columns well beyond the fill and drain of up to
-  // 2 x 192 steps.
+  // At least 32 sequences, over columns well beyond the fill and drain of up
+  // to 2 x 192 steps.  (rot_apply_f32 keeps k <= 41 on the column stream
+  // where it applies: 8192 x 8192, k = 41, 1.78 ms against 1.82.)
   return k >= 32 && n >= 1024 && m >= 1 && m < (int64_t(1) << 31) && n < (int64_t(1) << 30);
 }
 
 rot_status pipe_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C, int64_t ldc,
                           const float* S, int64_t lds, cudaStream_t s) {
-  // The first k32 = 32*floor(k/32) sequences run as passes of whole lanes
-  // of sequences, as even as possible (a pass of 32 stages costs almost as
-  // much as one of 64); the k - k32 left over follow on the column stream,
-  // or the wavefront kernel where the stream does not apply.  Each pass
-  // applies its sequences entirely before the next, as Algorithm 2 does.
+  // Passes of whole lanes of sequences (32 stages per lane of the group),
+  // as even as possible.  The r = k mod 32 left over either fill one more,
+  // part-filled lane (its stages past k pass their values through) or run
+  // on the column stream afterwards, whichever measured faster: a pass costs
+  // far less per sequence the more stages it has (8192 x 8192: 32 stages
+  // 1.34 ms, 64 1.55, 96 1.94, 192 2.73), a part-filled one 7-17 % more than
+  // a full one (64: 1.82), and the stream about 0.3 ms per 8 sequences.  So
+  // one more lane for r >= 22 (k = 95: 2.53 ms, against 3.0 with 31 on the
+  // stream), and for r >= 10 after a single lane (k = 42..63, 1.82 ms
+  // against 1.81-2.69), the stream otherwise (k = 65: 1.79 ms against 2.53).
+  // Each pass applies its sequences entirely before the next, as Algorithm
+  // 2 does.
   // Seven rows per warp: 8192 rows then make 1171 warps, 1.93 per SM
   // subpartition of a GB300 (eight rows: 1.68, so the busiest subpartitions
   // would carry two warps of 8 rows while others idle).
   constexpr int R = 7;
-  const int64_t units = k / 32;
+  const int64_t r = k % 32;
+  const bool round_up = r >= 22 || (k / 32 == 1 && r >= 10);
+  const int64_t units = k / 32 + (round_up ? 1 : 0);
+  const int64_t kpipe = round_up ? k : k - r;                 // sequences the passes apply
   const int64_t npass = (units + kPMaxSpl - 1) / kPMaxSpl;
   const int64_t KSmax = 32 * ((units + npass - 1) / npass);              // stages of the widest pass
   PipeScratch<float> ps;
@@ -513,9 +529,10 @@ rot_status pipe_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda
   for (int64_t gi = 0; gi < npass && st == ROT_OK; ++gi) {
     const int64_t left = units - p0 / 32;                     // lanes of sequences still to apply
     const int spl = (int)((left + (npass - gi) - 1) / (npass - gi));
-    const int kp = 32 * spl;
+    const int KS = 32 * spl;
+    const int kp = (int)std::min<int64_t>(KS, kpipe - p0);    // short only in the last pass
     int NT = 0;
-    st = pipe_table<float>(n, kp, kp, C + p0 * ldc, ldc, S + p0 * lds, lds, ps, s, &NT);
+    st = pipe_table<float>(n, kp, KS, C + p0 * ldc, ldc, S + p0 * lds, lds, ps, s, &NT);
     if (st != ROT_OK) break;
     const int tr = trace_begin(ROT_KERNEL_PIPE_F32, m * (n - 1) * kp, s);
     cudaError_t e;
@@ -535,14 +552,24 @@ rot_status pipe_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda
   if (st == ROT_OK) record_status_async(ps.status, s);
   cudaFreeAsync(ps.base, s);
   if (st != ROT_OK || p0 == k) return st;
-  const int64_t r = k - p0;
-  if (stream_fits<float>(m, n, r, A, lda))
-    return stream_apply<float>(m, n, r, A, lda, C + p0 * ldc, ldc, S + p0 * lds, lds, s);
-  return wave_apply_f32(m, n, r, A, lda, C + p0 * ldc, ldc, S + p0 * lds, lds, s, WaveOptions{});
+  if (stream_fits<float>(m, n, k - p0, A, lda))
+    return stream_apply<float>(m, n, k - p0, A, lda, C + p0 * ldc, ldc, S + p0 * lds, lds, s);
+  return wave_apply_f32(m, n, k - p0, A, lda, C + p0 * ldc, ldc, S + p0 * lds, lds, s, WaveOptions{});
 }
 
 rot_status apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C, int64_t ldc,
                      const double* S, int64_t lds, cudaStream_t s) {
+  if (k > 32 && k <= kF64ChunkedMaxK && pipe_f64_fits(m, n, 32)) {
+    // Chunks of up to 32 sequences, each applied entirely before the next
+    // (Algorithm 2's order), each on the lane pipeline (or, for one or two
+    // left over, the column stream).
+    for (int64_t p0 = 0; p0 < k; p0 += 32) {
+      const rot_status st = apply_f64(m, n, std::min<int64_t>(32, k - p0), A, lda, C + p0 * ldc, ldc,
+                                      S + p0 * lds, lds, s);
+      if (st != ROT_OK) return st;
+    }
+    return ROT_OK;
+  }
   if (pipe_f64_fits(m, n, k)) return pipe_apply_f64(m, n, k, A, lda, C, ldc, S, lds, s);
   if (stream_fits<double>(m, n, k, A, lda)) return stream_apply<double>(m, n, k, A, lda, C, ldc, S, lds, s);
   // The tiling the autotuner recorded for this shape (rot_batch_autotune on

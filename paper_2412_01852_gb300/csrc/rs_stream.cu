@@ -1,6 +1,6 @@
 // rs_stream.cu -- host side of the single-p-block column stream
-// (rs_stream.cuh).  rot_apply_f32 takes it for k <= 48 and rot_apply for
-// k <= 16, as passes of at most 8 sequences in sequence order (Algorithm 2
+// (rs_stream.cuh).  rot_apply_f32 takes it for k <= 41 (k <= 48 where the
+// lane pipeline does not apply) and rot_apply for k <= 16, as passes of at most 8 sequences in sequence order (Algorithm 2
 // applies sequence p entirely before p+1, so the passes compute the same
 // thing).  Measured at 8192 x 8192: a pass of 8 sequences takes 0.30 ms in
 // FP32 and 8.9 ms in FP64, where the wavefront kernel takes 2.0-2.3 ms

@@ -1,6 +1,7 @@
-"""The lane pipeline (rs_pipe.cu).  FP32: rot_apply_f32 takes it for k >= 32
-and n >= 1024 (where the column stream does not); FP64: rot_apply (and
-rot_apply_left) for 3 <= k <= 32 and n >= 256.  FP32 cases: bit-exact against
+"""The lane pipeline (rs_pipe.cu).  FP32: rot_apply_f32 takes it for k >= 42
+and n >= 1024 (and for k >= 32 where the column stream does not apply);
+FP64: rot_apply (and rot_apply_left) for 3 <= k <= 64 and n >= 256, above 32
+sequences in chunks of 32.  FP32 cases: bit-exact against
 the FP32 oracle on ragged row counts, padded leading dimensions, every pass
 width (32 .. 192 sequences), several passes (k = 224, 384, 448), the k mod 32
 sequences left over (on the column stream or the wavefront kernel), signed
@@ -48,7 +49,10 @@ CASES = [  # m, n, k, lda slack
     (40, 1057, 160, 1), (31, 4096, 128, 0), (257, 1024, 192, 7), (8, 1024, 224, 0), (64, 1030, 384, 2),
     (1, 1024, 32, 0), (7, 1031, 64, 0), (64, 1030, 448, 0),
     # k not a multiple of 32: the rest on the column stream (m >= 64) or the wavefront kernel
-    (70, 1100, 70, 0), (65, 1024, 100, 3), (20, 1024, 45, 0), (100, 1200, 203, 0),
+    (70, 1100, 70, 0), (65, 1024, 100, 3), (20, 1024, 45, 0), (100, 1200, 203, 0), (40, 1024, 35, 2),
+    # or one more, part-filled lane of sequences (k mod 32 >= 22, or >= 10 after one lane)
+    (64, 1024, 42, 0), (80, 1100, 63, 1), (9, 1024, 86, 0), (66, 1030, 95, 0), (30, 1024, 191, 3),
+    (70, 1024, 223, 0),
 ]
 
 
@@ -73,6 +77,13 @@ CASES64 = [  # m, n, k, lda slack: FP64, 3 <= k <= 32, n >= 256 (groups of 4, 8,
     # the same k with an odd lda (no column stream): the last pass takes it
     (65, 300, 9, 0),
 ]
+
+
+# FP64, 32 < k <= 64: chunks of 32 sequences on the lane pipeline, the last
+# one or two on the column stream (m >= 64, an even lda) or the wavefront
+# kernel.
+CASES64 += [(64, 300, 33, 0), (70, 256, 34, 2), (40, 400, 40, 0), (100, 260, 61, 0), (33, 512, 64, 1),
+            (9, 300, 33, 0)]
 
 
 @pytest.mark.parametrize("m,n,k,slack", CASES64)
