@@ -749,7 +749,8 @@ def variant_line(args):
             per = {}
             for prec in ("f32", "f64"):
                 Ad = _dev_colmajor(torch, A.astype(np.float32) if prec == "f32" else A, dev)
-                ks = list(range(1, 65)) if prec == "f32" else list(range(1, 41)) + [48, 64, 80, 96]
+                ks = (list(range(1, 65)) + [65, 80, 86, 95, 96, 100, 128, 150, 160, 191, 192] if prec == "f32"
+                      else list(range(1, 41)) + [48, 64, 80, 96, 128, 160, 192])
                 row = {}
                 for kk in ks:
                     C, S = wl.rotations(n, kk, 6)
