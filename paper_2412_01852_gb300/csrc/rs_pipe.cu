@@ -503,21 +503,25 @@ rot_status pipe_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda
   // Passes of whole lanes of sequences (32 stages per lane of the group),
   // as even as possible.  The r = k mod 32 left over either fill one more,
   // part-filled lane (its stages past k pass their values through) or run
-  // on the column stream afterwards, whichever measured faster: a pass costs
-  // far less per sequence the more stages it has (8192 x 8192: 32 stages
-  // 1.34 ms, 64 1.55, 96 1.94, 192 2.73), a part-filled one 7-17 % more than
-  // a full one (64: 1.82), and the stream about 0.3 ms per 8 sequences.  So
-  // one more lane for r >= 22 (k = 95: 2.53 ms, against 3.0 with 31 on the
-  // stream), and for r >= 10 after a single lane (k = 42..63, 1.82 ms
-  // against 1.81-2.69), the stream otherwise (k = 65: 1.79 ms against 2.53).
-  // Each pass applies its sequences entirely before the next, as Algorithm
-  // 2 does.
+  // on the column stream afterwards, whichever measured faster.  At
+  // 8192 x 8192 a full pass takes 1.34 ms with 32 stages, 1.55 with 64,
+  // 1.94 with 96, 2.30 with 128, 2.64 with 160 and 2.87 with 192; a
+  // part-filled one costs more the wider it is (64: +17 %, 96: +29 %, 160
+  // and 192: +35 %: its tiles take every stage's predicate at every step);
+  // the stream takes about 0.3 ms per 8 sequences.  So one more lane when
+  // r reaches kRoundUp[u] after u whole lanes (k = 95: 2.53 ms, against 3.0
+  // with 31 on the stream; k = 42..63: 1.82 against up to 2.69), the stream
+  // otherwise (k = 65: 1.79 ms, against 2.53 as a part-filled pass of 96),
+  // and never past six lanes, where the extra lane would start a second
+  // pass.  Each pass applies its sequences entirely before the next, as
+  // Algorithm 2 does.
   // Seven rows per warp: 8192 rows then make 1171 warps, 1.93 per SM
   // subpartition of a GB300 (eight rows: 1.68, so the busiest subpartitions
   // would carry two warps of 8 rows while others idle).
   constexpr int R = 7;
-  const int64_t r = k % 32;
-  const bool round_up = r >= 22 || (k / 32 == 1 && r >= 10);
+  constexpr int kRoundUp[6] = {33, 10, 22, 25, 29, 30};     // r needed after u whole lanes (33: never)
+  const int64_t r = k % 32, u = k / 32;
+  const bool round_up = u < 6 && r >= kRoundUp[u];
   const int64_t units = k / 32 + (round_up ? 1 : 0);
   const int64_t kpipe = round_up ? k : k - r;                 // sequences the passes apply
   const int64_t npass = (units + kPMaxSpl - 1) / kPMaxSpl;
