@@ -22,7 +22,7 @@
 // zeros keep their sign and infinities stay.
 //
 // FP32 (k >= 32): one group, up to 192 stages per pass, 7 rows, 4 warps per
-// CTA.  FP64 (3 <= k <= 32, and chunks of 32 up to k = 64): GB300's FP64
+// CTA.  FP64 (3 <= k <= 32): GB300's FP64
 // unit takes as long for a warp instruction whatever its active lanes, so
 // every lane holds a stage: k is rounded up to a power of two KS and the warp
 // holds 32/KS independent groups; CTAs of one warp up to KS = 16, of 4 warps
@@ -43,11 +43,6 @@ namespace {
 
 constexpr int kPTC = 32;      // steps (columns) per tile
 constexpr int kPMaxSpl = 6;   // FP32 sequences per lane: 192 per pass
-// FP64 above 32 sequences: chunks of 32 on the lane pipeline up to here, the
-// wavefront kernel beyond (8192 x 8192: k = 33 16.4 ms against 24.7, k = 64
-// 30.5 against 32.3, k = 80 38.2 against 37.4; 2048 x 2048: k = 64 4.7
-// against 6.5, k = 96 6.9 against 7.0).
-constexpr int64_t kF64ChunkedMaxK = 64;
 
 // W: warps per CTA.
 template <typename T, int SPL, int G, int R, int W = 4>
@@ -563,21 +558,14 @@ rot_status pipe_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda
 
 rot_status apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C, int64_t ldc,
                      const double* S, int64_t lds, cudaStream_t s) {
-  if (k > 32 && k <= kF64ChunkedMaxK && pipe_f64_fits(m, n, 32)) {
-    // Chunks of up to 32 sequences, each applied entirely before the next
-    // (Algorithm 2's order), each on the lane pipeline (or, for one or two
-    // left over, the column stream).
-    for (int64_t p0 = 0; p0 < k; p0 += 32) {
-      const rot_status st = apply_f64(m, n, std::min<int64_t>(32, k - p0), A, lda, C + p0 * ldc, ldc,
-                                      S + p0 * lds, lds, s);
-      if (st != ROT_OK) return st;
-    }
-    return ROT_OK;
-  }
   if (pipe_f64_fits(m, n, k)) return pipe_apply_f64(m, n, k, A, lda, C, ldc, S, lds, s);
   if (stream_fits<double>(m, n, k, A, lda)) return stream_apply<double>(m, n, k, A, lda, C, ldc, S, lds, s);
-  // The tiling the autotuner recorded for this shape (rot_batch_autotune on
-  // a batch of this one problem), else the defaults.
+  // The wavefront kernel, with the tiling the autotuner recorded for this
+  // shape (rot_batch_autotune on a batch of this one problem), else the
+  // defaults (p-blocks as long as the resident warps allow, wave_apply).
+  // Above 32 sequences it beats the lane pipeline in chunks of 32 nearly
+  // everywhere (2048 x 2048, k = 64: 3.37 ms against 4.68; 8192 x 8192,
+  // k = 33: 15.0 against 16.5).
   rot_problem p{m, n, k, A, lda, C, ldc, S, lds};
   rot_tuning tu{};
   tuning_lookup(1, &p, &tu);

@@ -134,11 +134,39 @@ static constexpr int kmax_for() { return 16; }
 static constexpr int kNBT = 16;
 static constexpr int kWarps = 8;
 
+// Sequences per p-block when the caller leaves the choice to the library:
+// the longest of 16, 8 and 4 that still gives every resident warp a work
+// item (a 32-row chain in one p-block) at once, the rule the batched launch
+// uses.  Measured on GB300 (whole calls, FP64): 8192 x 8192 k = 192 83.3 ms
+// at 16 (84.1 at 4); 2048 x 2048 k = 192 9.09 at 16, 6.89 at 4; 512 rows x
+// 4096 columns k = 192 13.3 at 16, 7.23 at 4; 4096 x 4096 k = 96 15.0 at 16,
+// 11.3 at 4.
+template <typename T>
+static int default_K(int64_t m, int64_t k, int ctas_per_sm_req) {
+  using SM = WaveSmem<T, kmax_for<T>(), kNBT>;
+  auto kfn = wave_kernel<T, kmax_for<T>(), kNBT, kWarps, kOpRotate>;
+  const int smem = kWarps * SM::kWarpBytes;
+  int dev = 0, nsm = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+      cudaSuccess || smem_opt_in(reinterpret_cast<const void*>(kfn), smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kWarps * 32, smem) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    return kmax_for<T>();
+  }
+  const int per_sm = ctas_per_sm_req > 0 ? std::min(ctas_per_sm_req, occ) : occ;
+  const long long warps = (long long)nsm * per_sm * kWarps;
+  const long long chains = ceil_div(m, 32);
+  for (int K : {16, 8})
+    if (chains * ceil_div(k, K) >= warps) return K;
+  return 4;
+}
+
 template <typename T>
 rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
                       const T* S, int64_t lds, cudaStream_t stream, const WaveOptions& opt) {
   constexpr int KMAX = kmax_for<T>();
-  const WavePlan pl = plan_wave(m, n, k, KMAX, kNBT, opt.K, opt.NB, (int)sizeof(T), 32);
+  const int K_req = opt.K > 0 ? opt.K : default_K<T>(m, k, opt.ctas_per_sm);
+  const WavePlan pl = plan_wave(m, n, k, KMAX, kNBT, K_req, opt.NB, (int)sizeof(T), 32);
 
   // Scratch: [repacked (c,s) | done counters | ticket | status]
   const int64_t W2 = 2 * (int64_t)pl.kpad;

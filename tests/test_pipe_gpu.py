@@ -1,7 +1,6 @@
 """The lane pipeline (rs_pipe.cu).  FP32: rot_apply_f32 takes it for k >= 42
 and n >= 1024 (and for k >= 32 where the column stream does not apply);
-FP64: rot_apply (and rot_apply_left) for 3 <= k <= 64 and n >= 256, above 32
-sequences in chunks of 32.  FP32 cases: bit-exact against
+FP64: rot_apply (and rot_apply_left) for 3 <= k <= 32 and n >= 256.  FP32 cases: bit-exact against
 the FP32 oracle on ragged row counts, padded leading dimensions, every pass
 width (32 .. 192 sequences), several passes (k = 224, 384, 448), the k mod 32
 sequences left over (on the column stream or the wavefront kernel), signed
@@ -79,9 +78,8 @@ CASES64 = [  # m, n, k, lda slack: FP64, 3 <= k <= 32, n >= 256 (groups of 4, 8,
 ]
 
 
-# FP64, 32 < k <= 64: chunks of 32 sequences on the lane pipeline, the last
-# one or two on the column stream (m >= 64, an even lda) or the wavefront
-# kernel.
+# FP64 just past 32 sequences: the wavefront kernel with p-blocks as long as
+# the resident warps allow (short ones for these few rows).
 CASES64 += [(64, 300, 33, 0), (70, 256, 34, 2), (40, 400, 40, 0), (100, 260, 61, 0), (33, 512, 64, 1),
             (9, 300, 33, 0)]
 

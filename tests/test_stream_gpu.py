@@ -1,5 +1,5 @@
 """The column stream (one pass per 8 sequences) that rot_apply (k <= 16; the
-lane pipeline takes 3 <= k <= 64 when n >= 256) and rot_apply_f32 (k <= 41, or
+lane pipeline takes 3 <= k <= 32 when n >= 256) and rot_apply_f32 (k <= 41, or
 k <= 48 where the lane pipeline does not apply)
 take when A is TMA-addressable: bit-exact against the
 oracles on ragged shapes, padded leading dimensions, every k from 1 to 8 (so
