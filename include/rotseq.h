@@ -161,10 +161,12 @@ rot_status rot_apply_host(int64_t m, int64_t n, int64_t k, double* A_host, int64
  *   each call, the rest is overwritten.  Calls whose work overlaps on the GPU
  *   (different streams, or host threads racing on one device) race on it and
  *   give wrong results: order them on one stream or synchronize in between.
- *   Speed: this entry point always runs the wavefront kernel.  rot_apply
- *   picks faster kernels for few sequences (k <= 32), whose scratch is
- *   sized differently; at 8192 x 8192 with k = 8 this call takes about
- *   twice as long as rot_apply.  For k > 32 the two run the same kernel.
+ *   Speed: this entry point always runs the wavefront kernel, with the
+ *   p-block length rot_apply's wavefront kernel takes.  rot_apply picks
+ *   faster kernels for few sequences (k <= 32), whose scratch is sized
+ *   differently; at 8192 x 8192 with k = 8 this call takes about twice as
+ *   long as rot_apply.  For k > 32 the two run the same kernel with the same
+ *   tiling (unless the autotuner recorded one for rot_apply's shape).
  *   rot_last_error() names the failing CUDA call on ROT_ECUDA.
  */
 rot_status rot_apply_noalloc(int64_t m, int64_t n, int64_t k, double* A, int64_t lda,

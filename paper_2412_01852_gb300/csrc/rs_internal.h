@@ -31,6 +31,9 @@ struct WavePlan {
   long long total;
 };
 
+// Sequences per p-block of the FP64 wavefront kernel when the caller leaves
+// the choice to the library (rs_wave_host.cu).
+int wave_default_K_f64(int64_t m, int64_t k, int ctas_per_sm_req);
 WavePlan plan_wave(int64_t m, int64_t n, int64_t k, int kmax, int nbt, int K_req, int NB_req,
                    int elem_bytes, int rows_per_chain = 32);
 

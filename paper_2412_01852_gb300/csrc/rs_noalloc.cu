@@ -130,7 +130,9 @@ extern "C" rot_status rot_apply_noalloc(int64_t m, int64_t n, int64_t k, double*
   if (!A || !C || !S) return ROT_EINVAL;
 
   using T = double;
-  const rs::WavePlan pl = rs::plan_wave(m, n, k, kKMAX, kNBT, 0, 0, (int)sizeof(T));
+  // p-blocks as rot_apply's wavefront kernel takes them (longer ones while
+  // they still give every resident warp a work item)
+  const rs::WavePlan pl = rs::plan_wave(m, n, k, kKMAX, kNBT, rs::wave_default_K_f64(m, k, 0), 0, (int)sizeof(T));
   const int64_t W2 = 2 * (int64_t)pl.kpad;
   const size_t cs_bytes = (size_t)pl.cs_rows * W2 * sizeof(T);
   const size_t done_off = round_up(cs_bytes, 256);

@@ -161,6 +161,8 @@ static int default_K(int64_t m, int64_t k, int ctas_per_sm_req) {
   return 4;
 }
 
+int wave_default_K_f64(int64_t m, int64_t k, int ctas_per_sm_req) { return default_K<double>(m, k, ctas_per_sm_req); }
+
 template <typename T>
 rot_status wave_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
                       const T* S, int64_t lds, cudaStream_t stream, const WaveOptions& opt) {
