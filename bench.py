@@ -744,7 +744,7 @@ def variant_line(args):
             return float(np.median(ts))
 
         shapes = {}
-        for (m, n) in ((8192, 8192), (2048, 2048), (8192, 512)):
+        for (m, n) in ((8192, 8192), (4096, 4096), (2048, 2048), (8192, 512)):
             A = wl.matrix(m, n, 6)
             per = {}
             for prec in ("f32", "f64"):

@@ -487,10 +487,11 @@ rot_status pipe_table(int64_t n, int kp, int KS, const T* C, int64_t ldc, const 
 }  // namespace
 
 bool pipe_f32_fits(int64_t m, int64_t n, int64_t k) {
-  // At least 32 sequences, over columns well beyond the fill and drain of up
+  // At least 20 sequences, over columns well beyond the fill and drain of up
   // to 2 x 192 steps.  (rot_apply_f32 keeps k <= 41 on the column stream
-  // where it applies: 8192 x 8192, k = 41, 1.78 ms against 1.82.)
-  return k >= 32 && n >= 1024 && m >= 1 && m < (int64_t(1) << 31) && n < (int64_t(1) << 30);
+  // where it applies and the matrix has more than 4096 rows: 8192 x 8192,
+  // k = 41, 1.78 ms against 1.82.)
+  return k >= 20 && n >= 1024 && m >= 1 && m < (int64_t(1) << 31) && n < (int64_t(1) << 30);
 }
 
 rot_status pipe_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C, int64_t ldc,
@@ -508,15 +509,22 @@ rot_status pipe_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda
   // with 31 on the stream; k = 42..63: 1.82 against up to 2.69), the stream
   // otherwise (k = 65: 1.79 ms, against 2.53 as a part-filled pass of 96),
   // and never past six lanes, where the extra lane would start a second
-  // pass.  Each pass applies its sequences entirely before the next, as
+  // pass.  With no whole lane (20 <= k < 32, few rows) the one pass is
+  // part-filled.  Each pass applies its sequences entirely before the next, as
   // Algorithm 2 does.
   // Seven rows per warp: 8192 rows then make 1171 warps, 1.93 per SM
   // subpartition of a GB300 (eight rows: 1.68, so the busiest subpartitions
   // would carry two warps of 8 rows while others idle).
   constexpr int R = 7;
-  constexpr int kRoundUp[6] = {33, 10, 22, 25, 29, 30};     // r needed after u whole lanes (33: never)
+  // r needed after u whole lanes (33: never); below one lane, only where
+  // rot_apply_f32 sends k >= 20 here (up to 4096 rows)
+  constexpr int kRoundUp[6] = {20, 10, 22, 25, 29, 30};
   const int64_t r = k % 32, u = k / 32;
-  const bool round_up = u < 6 && r >= kRoundUp[u];
+  // With few rows the stream is relatively slower, so after one lane the
+  // part-filled pass pays from r = 7 (4096 x 4096, k = 39: 0.64 ms against
+  // 0.71 as 32 stages and 7 on the stream).
+  const int r_min = (u == 1 && m <= 4096) ? 7 : (u < 6 ? kRoundUp[u] : 33);
+  const bool round_up = r >= r_min;
   const int64_t units = k / 32 + (round_up ? 1 : 0);
   const int64_t kpipe = round_up ? k : k - r;                 // sequences the passes apply
   const int64_t npass = (units + kPMaxSpl - 1) / kPMaxSpl;

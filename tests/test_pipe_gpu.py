@@ -1,5 +1,6 @@
-"""The lane pipeline (rs_pipe.cu).  FP32: rot_apply_f32 takes it for k >= 42
-and n >= 1024 (and for k >= 32 where the column stream does not apply);
+"""The lane pipeline (rs_pipe.cu).  FP32: rot_apply_f32 takes it for n >= 1024
+and k >= 42, or k >= 20 with at most 4096 rows (and for k >= 20 where the
+column stream does not apply);
 FP64: rot_apply (and rot_apply_left) for 3 <= k <= 32 and n >= 256.  FP32 cases: bit-exact against
 the FP32 oracle on ragged row counts, padded leading dimensions, every pass
 width (32 .. 192 sequences), several passes (k = 224, 384, 448), the k mod 32
@@ -52,6 +53,8 @@ CASES = [  # m, n, k, lda slack
     # or one more, part-filled lane of sequences (k mod 32 >= 22, or >= 10 after one lane)
     (64, 1024, 42, 0), (80, 1100, 63, 1), (9, 1024, 86, 0), (66, 1030, 95, 0), (30, 1024, 191, 3),
     (70, 1024, 223, 0),
+    # 20 <= k < 32 with few rows: a single part-filled pass
+    (64, 1024, 20, 0), (100, 1100, 31, 3), (9, 1024, 24, 0),
 ]
 
 
