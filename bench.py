@@ -720,10 +720,10 @@ def variant_line(args):
         return line
 
     if args.variant == "k-sweep":
-        # Whole calls of rot_apply (FP64) and rot_apply_f32 over k, on three
-        # shapes, to show how the dispatch (column stream, lane pipeline in
-        # passes or chunks, wavefront kernel) behaves between the fixed k of
-        # the other variants.  Median of four calls per k, each after an L2
+        # Whole calls of rot_apply (FP64) and rot_apply_f32 over k, on four
+        # shapes (FP64 on seven), to show how the dispatch (column stream,
+        # lane pipeline in passes, wavefront kernel) behaves between the fixed
+        # k of the other variants.  Median of four calls per k, each after an L2
         # flush (a 256 MiB write), CUDA events around the call.
         flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
 
@@ -744,10 +744,15 @@ def variant_line(args):
             return float(np.median(ts))
 
         shapes = {}
-        for (m, n) in ((8192, 8192), (4096, 4096), (2048, 2048), (8192, 512)):
+        # FP64 also on 4864 x 8192 (152 strips of 32 rows, one per SM),
+        # 1024 x 8192 and 16384 x 2048 (512 strips), around the split
+        # stream's strip thresholds.
+        for (m, n, precs) in ((8192, 8192, ("f32", "f64")), (4096, 4096, ("f32", "f64")),
+                              (2048, 2048, ("f32", "f64")), (8192, 512, ("f32", "f64")), (4864, 8192, ("f64",)),
+                              (1024, 8192, ("f64",)), (16384, 2048, ("f64",))):
             A = wl.matrix(m, n, 6)
             per = {}
-            for prec in ("f32", "f64"):
+            for prec in precs:
                 Ad = _dev_colmajor(torch, A.astype(np.float32) if prec == "f32" else A, dev)
                 ks = (list(range(1, 65)) + [65, 80, 86, 95, 96, 100, 128, 150, 160, 191, 192] if prec == "f32"
                       else list(range(1, 41)) + [48, 64, 80, 96, 128, 160, 192])

@@ -564,8 +564,32 @@ rot_status pipe_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda
   return wave_apply_f32(m, n, k - p0, A, lda, C + p0 * ldc, ldc, S + p0 * lds, lds, s, WaveOptions{});
 }
 
+// SMs of the current device (0 if it cannot be read).
+static int device_sms() {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nsm;
+}
+
 rot_status apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C, int64_t ldc,
                      const double* S, int64_t lds, cudaStream_t s) {
+  // The split column stream (passes of up to 4 sequences, two warps a
+  // sequence per 32-row strip) while its strips fit one CTA per SM (each
+  // chain then waits only on its own latency), or for three sequences with
+  // two strips per SM.  Measured against the lane pipeline (rot_apply, the
+  // same box, median of 5 calls): k = 3..8 at 4096 x 4096 0.81-1.59 ms
+  // against 1.18-1.83, at 1024 x 8192 1.48-3.02 against 2.05-3.35; k = 3 at
+  // 8192 x 8192 1.92 against 2.37, at 6144 x 6144 1.47 against 1.78.  With
+  // two strips per SM from k = 4 on the pipeline is ahead (8192 x 8192,
+  // k = 4: 2.42 against 2.38; k = 8: 4.73 against 4.02).
+  const int64_t strips = (m + 31) / 32;
+  const int64_t nsm = device_sms();
+  if (stream_fits<double>(m, n, k, A, lda) && ((k <= 8 && strips <= nsm) || (k == 3 && strips <= 2 * nsm)))
+    return stream_apply<double>(m, n, k, A, lda, C, ldc, S, lds, s);
   if (pipe_f64_fits(m, n, k)) return pipe_apply_f64(m, n, k, A, lda, C, ldc, S, lds, s);
   if (stream_fits<double>(m, n, k, A, lda)) return stream_apply<double>(m, n, k, A, lda, C, ldc, S, lds, s);
   // The wavefront kernel, with the tiling the autotuner recorded for this
@@ -589,30 +613,70 @@ bool pipe_f64_fits(int64_t m, int64_t n, int64_t k) {
   return k >= 3 && k <= 32 && n >= 256 && m >= 1 && m < (int64_t(1) << 31) && n < (int64_t(1) << 30);
 }
 
-// FP64 passes for k sequences: stages per group and sequences of each pass
-// (at most 3); with tail_on_stream the last sequence is left to the caller.
-static int pipe_f64_passes(int64_t k, bool tail_on_stream, int (&KS)[4], int (&kp)[4]) {
-  // Every lane holds one stage, so a pass costs its KS (k rounded up to a
-  // power of two) whatever the sequences it applies.  So k runs as passes of
-  // powers of two from 32 down to 4 (the binary digits of k rounded up to a
-  // multiple of 4), the last one short by that rounding; a single sequence
-  // left over (k = 4j + 1) goes to the column stream when it applies.
-  const int64_t kt = tail_on_stream ? k - 1 : k;
-  const int64_t q = (kt + 3) / 4 * 4;
+// FP64 passes for k sequences: the stages per group and the sequences of
+// each lane-pipeline pass (np of them, at most 3), and the sequences left to
+// the split column stream at the end (tail, at most 7).
+struct PipePlan64 {
   int np = 0;
-  for (int b = 32; b >= 4; b /= 2)
-    if (q & b) {
-      KS[np] = b;
-      kp[np] = b;
-      ++np;
+  int KS[4] = {0, 0, 0, 0};
+  int kp[4] = {0, 0, 0, 0};
+  int tail = 0;
+};
+
+static PipePlan64 pipe_f64_plan(int64_t m, int64_t k, bool tail_ok, int64_t nsm) {
+  // Every lane holds one stage, so a pass costs its KS (a power of two from
+  // 4 to 32) whatever the sequences it applies, and a pass short of its KS
+  // more (its stages past k pass values through: 4096 x 4096, KS = 32 with
+  // 21..31 sequences 5.33 ms, with 32 4.55).
+  PipePlan64 p;
+  auto pass = [&](int KS, int64_t kp) {
+    p.KS[p.np] = KS;
+    p.kp[p.np] = (int)kp;
+    ++p.np;
+  };
+  const int64_t strips = (m + 31) / 32;
+  if (tail_ok && nsm > 0 && strips <= nsm) {
+    // At most one 32-row strip per SM: the split stream takes up to 7
+    // sequences for less than a pass of 8 (4096 x 4096: 5..7 in 1.42-1.55
+    // ms, a pass of 8 1.76; 4864 x 8192: 2.67-2.94 against 3.34).  So full
+    // passes of 8, 16 and 32 for the multiple of 8, the rest on the stream.
+    // From 29 sequences on and up to 4096 rows one pass of 32 short of its
+    // stages is cheaper (4096 x 4096: 5.34 ms against 5.96-6.11 for
+    // k = 29..31; 2048 x 2048: 2.77 against 3.02-3.08), with more rows it is
+    // not (4864 x 8192: 15.6 against 11.7-12.0).
+    if (k >= 29 && m <= 4096) {
+      pass(32, k);
+      return p;
     }
-  kp[np - 1] -= (int)(q - kt);
-  return np;
+    const int64_t q = k / 8 * 8;
+    for (int b = 32; b >= 8; b /= 2)
+      if (q & b) pass(b, b);
+    p.tail = (int)(k - q);
+    return p;
+  }
+  // Otherwise the FP64 units bound every pass (8192 x 8192: KS = 4, 8, 16, 32
+  // take 2.37, 4.01, 7.79, 15.3 ms) and k runs as passes of powers of two
+  // from 32 down to 4 (the binary digits of k rounded up to a multiple of 4),
+  // the last one short by that rounding.  A remainder of 1 (k = 4j + 1) or,
+  // past a pass of 8, of 2 goes to the split stream (1.25 and 1.60 ms), and
+  // one of 3 too while there are at most two strips per SM (1.92 ms, where
+  // strips run in several rounds it is slower than a pass of 4).
+  if (tail_ok) {
+    if (k % 4 == 1) p.tail = 1;
+    else if (k >= 10 && k % 8 == 2) p.tail = 2;
+    else if (k >= 10 && k % 8 == 3 && nsm > 0 && strips <= 2 * nsm) p.tail = 3;
+  }
+  const int64_t kt = k - p.tail;
+  const int64_t q = (kt + 3) / 4 * 4;
+  for (int b = 32; b >= 4; b /= 2)
+    if (q & b) pass(b, b);
+  if (p.np > 0) p.kp[p.np - 1] -= (int)(q - kt);
+  return p;
 }
 
 rot_status pipe_apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t lda, const double* C, int64_t ldc,
                           const double* S, int64_t lds, cudaStream_t s) {
-  // Passes (pipe_f64_passes), each applying its sequences entirely before
+  // Passes (pipe_f64_plan), each applying its sequences entirely before
   // the next, as Algorithm 2 does.  Every lane holds one stage of a group
   // of KS lanes (stages past a pass's sequences pass their values through),
   // 32/KS groups per warp, about 8 rows per warp.  Up to 16 stages a CTA is
@@ -621,35 +685,40 @@ rot_status pipe_apply_f64(int64_t m, int64_t n, int64_t k, double* A, int64_t ld
   // SM's FP64 unit takes time in proportion to its rows (k = 8: 4.86 ->
   // 4.09 ms, k = 16: 9.33 -> 8.04 ms at 8192 x 8192).  At 32 stages the
   // table tiles leave room for only 4 one-warp CTAs per SM (18.4 ms against
-  // 16.3).
-  const bool tail = k % 4 == 1 && stream_fits<double>(m, n, 1, A, lda);
-  int KS[4], kp[4];
-  const int np = pipe_f64_passes(k, tail, KS, kp);
-  PipeScratch<double> ps;
-  rot_status st = pipe_scratch<double>(n, KS[0], s, &ps);
-  if (st != ROT_OK) return st;
+  // 16.3).  The plan leaves up to 7 sequences to the split column stream
+  // where it applies (A 16-byte aligned, an even lda, m and n >= 64).
+  const PipePlan64 plan = pipe_f64_plan(m, k, stream_fits<double>(m, n, 4, A, lda), device_sms());
+  const int np = plan.np;
+  const int* KS = plan.KS;
+  const int* kp = plan.kp;
   int64_t p0 = 0;
-  for (int i = 0; i < np && st == ROT_OK; ++i) {
-    int NT = 0;
-    st = pipe_table<double>(n, kp[i], KS[i], C + p0 * ldc, ldc, S + p0 * lds, lds, ps, s, &NT);
-    if (st != ROT_OK) break;
-    const int tr = trace_begin(ROT_KERNEL_PIPE_F64, m * (n - 1) * kp[i], s);
-    cudaError_t e;
-    switch (KS[i]) {
-      case 4: e = launch_pipe<double, 1, 8, 1, 1>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
-      case 8: e = launch_pipe<double, 1, 4, 2, 1>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
-      case 16: e = launch_pipe<double, 1, 2, 4, 1>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
-      default: e = launch_pipe<double, 1, 1, 7, 4>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
+  rot_status st = ROT_OK;
+  if (np > 0) {
+    PipeScratch<double> ps;
+    st = pipe_scratch<double>(n, KS[0], s, &ps);
+    if (st != ROT_OK) return st;
+    for (int i = 0; i < np && st == ROT_OK; ++i) {
+      int NT = 0;
+      st = pipe_table<double>(n, kp[i], KS[i], C + p0 * ldc, ldc, S + p0 * lds, lds, ps, s, &NT);
+      if (st != ROT_OK) break;
+      const int tr = trace_begin(ROT_KERNEL_PIPE_F64, m * (n - 1) * kp[i], s);
+      cudaError_t e;
+      switch (KS[i]) {
+        case 4: e = launch_pipe<double, 1, 8, 1, 1>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
+        case 8: e = launch_pipe<double, 1, 4, 2, 1>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
+        case 16: e = launch_pipe<double, 1, 2, 4, 1>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
+        default: e = launch_pipe<double, 1, 1, 7, 4>(ps.tab, NT, A, lda, (int)m, (int)n, kp[i], ps.status, s); break;
+      }
+      trace_end(tr, s);
+      if (e != cudaSuccess) { st = cuda_failed(e, "pipe_f64: kernel launch"); break; }
+      count_launches(2);
+      p0 += kp[i];
     }
-    trace_end(tr, s);
-    if (e != cudaSuccess) { st = cuda_failed(e, "pipe_f64: kernel launch"); break; }
-    count_launches(2);
-    p0 += kp[i];
+    if (st == ROT_OK) record_status_async(ps.status, s);
+    cudaFreeAsync(ps.base, s);
   }
-  if (st == ROT_OK) record_status_async(ps.status, s);
-  cudaFreeAsync(ps.base, s);
-  if (st != ROT_OK || !tail) return st;
-  return stream_apply<double>(m, n, 1, A, lda, C + p0 * ldc, ldc, S + p0 * lds, lds, s);
+  if (st != ROT_OK || plan.tail == 0) return st;
+  return stream_apply<double>(m, n, plan.tail, A, lda, C + p0 * ldc, ldc, S + p0 * lds, lds, s);
 }
 
 }  // namespace rs

@@ -151,26 +151,27 @@ stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
     __syncwarp();                                // every lane has read the stage
     if (lane == 0 && t + S < ntiles) issue(t + S);
   }
-  // On a timeout, let the copies still in flight land before leaving.
+  // On a timeout, let the copies still in flight (from tile t on) land before
+  // leaving; one that already landed returns at once.
   if (t < ntiles && lane == 0) {
-    for (int r = t + 1; r < ntiles && r < t + S; ++r) (void)mbar_wait_bounded(&bar[r % S], (uint32_t)(r / S) & 1u);
+    for (int r = t; r < ntiles && r < t + S; ++r) (void)mbar_wait_bounded(&bar[r % S], (uint32_t)(r / S) & 1u);
   }
 }
 
 // ---------------------------------------------------------------------------
-// FP64, one or two sequences: the column stream split over warps.
+// FP64, one to four sequences: the column stream split over warps.
 //
 // GB300's FP64 unit belongs to an SM sub-partition and takes 64 cycles for a
 // warp instruction, whatever its active lanes, and a row's chain of
 // rotations is sequential: column after column, x <- fma(c, y, -RN(s*x)).
 // Issued in order, every other FP64 instruction of the warp (the finished
 // column fma(c, x, RN(s*y)) and its product) delays that chain.  So each warp
-// here carries only two FP64 instructions a column:
-//   k = 1: warp 0 the chain, handing each column's incoming x to warp 1,
-//          which forms the finished column;
-//   k = 2: warp 0 the chain of sequence 0, warp 1 its finished columns,
-//          warp 2 the chain of sequence 1 over those columns, warp 3 their
-//          finished columns (the result).
+// here carries only two FP64 instructions a column, two warps a sequence:
+// warp 2p the chain of sequence p, handing each column's incoming x to warp
+// 2p + 1, which forms the finished column from it and sequence p's input
+// column (A itself for p = 0, else warp 2p - 1's finished columns); warp
+// 2p + 1's columns go to the chain of sequence p + 1, and the last warp's
+// are the result.
 // Every element sees rotate_dmul's operations on the same operands, in the
 // same order: bit-identical.  Values pass between warps through rings of
 // RING tiles of CB values per lane in shared memory (ready/free barriers);
@@ -183,18 +184,33 @@ stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
 // warp's own dependent chain is the bound): k = 1 1.13 ms, 280 cycles a
 // column (one warp per strip: 1.26 ms); k = 2 1.48 ms (one warp: 2.32 ms; two
 // warps, one per sequence: 1.83 ms).  The chain's product on the integer pipe
-// (dmul_int) was slower: 1.67 ms at k = 1 (two-warp build).
+// (dmul_int) was slower: 1.67 ms at k = 1 (two-warp build).  Whole calls of
+// rot_apply at k = 3 and 4: 0.80 and 0.85 ms at 4096 x 4096 (one strip per
+// SM), 1.90 and 2.37 ms at 8192 x 8192 (two strips on most SMs, whose FP64
+// units then bound it).
 template <int KR>
 struct SplitShape {
   using SS = StreamShape<double, KR, 1>;
   static constexpr int NW = 2 * KR;                        // warps
   static constexpr int NRING = NW - 1;                     // rings between consecutive warps
   static constexpr int RING = KR == 1 ? 4 : 2;             // tiles per ring
-  static constexpr int kRingTile = SS::CB * 32 * (int)sizeof(double);
-  static constexpr int kRingOff = SS::S * SS::kStage;
+  // A warp starts a tile once the warp before it has handed the whole tile
+  // over, so the last warp trails the first by about a tile per chain; the
+  // S stages cover that lag and the copies' latency.  From three sequences
+  // on, tiles of 16 columns keep 8 stages and the rings within half an SM's
+  // shared memory (two CTAs per SM).
+  static constexpr int CB = KR <= 2 ? SS::CB : 16;         // columns per tile
+  static constexpr int S = 8;                              // TMA stages
+  static constexpr int KP = SS::KP;
+  static constexpr int kABytes = 32 * CB * (int)sizeof(double);
+  static constexpr int kCsBytes = CB * 2 * KP * (int)sizeof(double);
+  static constexpr int kAStage = (kABytes + 127) / 128 * 128;
+  static constexpr int kStage = kAStage + (kCsBytes + 127) / 128 * 128;
+  static constexpr int kRingTile = CB * 32 * (int)sizeof(double);
+  static constexpr int kRingOff = S * kStage;
   static constexpr int kBarOff = kRingOff + NRING * RING * kRingTile;
   // barriers: full[S], consumed[S], ready[NRING][RING], free[NRING][RING]; then the abort flag
-  static constexpr int kSmem = kBarOff + (2 * SS::S + 2 * NRING * RING) * 8 + 16;
+  static constexpr int kSmem = kBarOff + (2 * S + 2 * NRING * RING) * 8 + 16;
 };
 
 // Shared state of one CTA of stream_split_kernel.
@@ -218,15 +234,14 @@ struct SplitCta {
 // loads feeding them and the hand-off store).
 template <int KR, int W>
 __device__ __forceinline__ void split_role(const SplitCta& X) {
-  using SS = StreamShape<double, KR, 1>;
   using SP = SplitShape<KR>;
   using V2 = typename Pair<double>::type;
-  constexpr int CB = SS::CB, S = SS::S, KP = SS::KP, RING = SP::RING, NW = SP::NW;
+  constexpr int CB = SP::CB, S = SP::S, KP = SP::KP, RING = SP::RING, NW = SP::NW;
   constexpr bool kChain = (W & 1) == 0;         // a chain (else finished columns)
   constexpr int kSeq = W / 2;                   // its sequence
   constexpr bool kWrites = W < NW - 1;          // hands values to the next warp
-  constexpr bool kReadsPrev = W > 0;
-  constexpr bool kReadsR1 = KR == 2 && W == 3;  // sequence 1's input columns
+  constexpr bool kReadsPrev = W > 0;            // ring W-1: the previous warp's hand-off
+  constexpr bool kReadsIn = !kChain && kSeq > 0;  // ring W-2: its sequence's input columns
   constexpr bool kLast = W == NW - 1;
   const int lane = X.lane, n = X.n;
   auto ring = [&](int g, int q) {
@@ -243,11 +258,11 @@ __device__ __forceinline__ void split_role(const SplitCta& X) {
   };
   auto issue = [&](int t) {
     const int s = t % S;
-    unsigned char* st = X.smem + s * SS::kStage;
+    unsigned char* st = X.smem + s * SP::kStage;
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&X.full[s], SS::kABytes + SS::kCsBytes);
+    mbar_arrive_expect_tx(&X.full[s], SP::kABytes + SP::kCsBytes);
     tma_load_2d(st, X.amap, &X.full[s], X.c * 32, t * CB);
-    tma_load_2d(st + SS::kAStage, X.csmap, &X.full[s], 0, t * CB - 1);
+    tma_load_2d(st + SP::kAStage, X.csmap, &X.full[s], 0, t * CB - 1);
   };
   const bool rowok = X.c * 32 + lane < X.m;
   double x = 0.0;                               // a chain's carried value
@@ -259,13 +274,13 @@ __device__ __forceinline__ void split_role(const SplitCta& X) {
     const uint32_t use = (uint32_t)(t / RING);
     if (!wait(&X.full[s], (uint32_t)(t / S) & 1u)) break;
     if (kReadsPrev && !wait(&X.ready[(W - 1) * RING + q], use & 1u)) break;
-    if (kReadsR1 && !wait(&X.ready[1 * RING + q], use & 1u)) break;
+    if (kReadsIn && !wait(&X.ready[(W - 2) * RING + q], use & 1u)) break;
     if (kWrites && t >= RING && !wait(&X.freed[W * RING + q], (use - 1) & 1u)) break;
-    const double* at = reinterpret_cast<const double*>(X.smem + s * SS::kStage) + lane;
-    const V2* cs = reinterpret_cast<const V2*>(X.smem + s * SS::kStage + SS::kAStage) + kSeq;
+    const double* at = reinterpret_cast<const double*>(X.smem + s * SP::kStage) + lane;
+    const V2* cs = reinterpret_cast<const V2*>(X.smem + s * SP::kStage + SP::kAStage) + kSeq;
     double* out = kWrites ? ring(W, q) : nullptr;
     const double* in = kReadsPrev ? ring(W - 1, q) : nullptr;
-    const double* in1 = kReadsR1 ? ring(1, q) : nullptr;
+    const double* in1 = kReadsIn ? ring(W - 2, q) : nullptr;
     // Sequence kSeq takes its input column j + 1 at wave w = j + kSeq; its
     // rotation (j, j+1) has the pair of wave w, index kSeq.
     const int j0 = t * CB - 1 - kSeq;
@@ -300,7 +315,7 @@ __device__ __forceinline__ void split_role(const SplitCta& X) {
     }
     if constexpr (kWrites) mbar_arrive(&X.ready[W * RING + q]);
     if constexpr (kReadsPrev) mbar_arrive(&X.freed[(W - 1) * RING + q]);
-    if constexpr (kReadsR1) mbar_arrive(&X.freed[1 * RING + q]);
+    if constexpr (kReadsIn) mbar_arrive(&X.freed[(W - 2) * RING + q]);
     if constexpr (!kLast) {
       mbar_arrive(&X.consumed[s]);
     } else {
@@ -314,19 +329,19 @@ __device__ __forceinline__ void split_role(const SplitCta& X) {
       }
     }
   }
-  // On a timeout, let the copies still in flight land before leaving.
+  // On a timeout, let the copies still in flight (from tile t on) land before
+  // leaving; one that already landed returns at once.
   if (kLast && t < X.ntiles && lane == 0)
-    for (int u = t + 1; u < issued; ++u) (void)mbar_wait_bounded(&X.full[u % S], (uint32_t)(u / S) & 1u);
+    for (int u = t; u < issued; ++u) (void)mbar_wait_bounded(&X.full[u % S], (uint32_t)(u / S) & 1u);
 }
 
 template <int KR>
 __global__ void __launch_bounds__(64 * KR)
 stream_split_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap csmap, double* A,
                     int64_t lda, int m, int n, int* status) {
-  static_assert(KR == 1 || KR == 2, "one or two sequences");
-  using SS = StreamShape<double, KR, 1>;
+  static_assert(KR >= 1 && KR <= 4, "one to four sequences");
   using SP = SplitShape<KR>;
-  constexpr int CB = SS::CB, S = SS::S, RING = SP::RING, NW = SP::NW, NRING = SP::NRING;
+  constexpr int CB = SP::CB, S = SP::S, RING = SP::RING, NW = SP::NW, NRING = SP::NRING;
   extern __shared__ __align__(1024) unsigned char smem[];
   SplitCta X;
   X.amap = &amap;
@@ -355,29 +370,31 @@ stream_split_kernel(const __grid_constant__ CUtensorMap amap, const __grid_const
     for (int g = 0; g < NRING; ++g)
       for (int q = 0; q < RING; ++q) {
         mbar_init(&X.ready[g * RING + q], 32);
-        // ring 1 of k = 2 (sequence 0's finished columns) is read by warps 2 and 3
-        mbar_init(&X.freed[g * RING + q], (KR == 2 && g == 1) ? 64 : 32);
+        // an odd ring (a sequence's finished columns) is read by the next
+        // sequence's two warps, an even one (a chain's hand-off) by one
+        mbar_init(&X.freed[g * RING + q], (g & 1) ? 64 : 32);
       }
     *X.abort_flag = 0;
     fence_mbarrier_init();
     for (int t = 0; t < S && t < X.ntiles; ++t) {
-      unsigned char* st = smem + t * SS::kStage;
+      unsigned char* st = smem + t * SP::kStage;
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&X.full[t], SS::kABytes + SS::kCsBytes);
+      mbar_arrive_expect_tx(&X.full[t], SP::kABytes + SP::kCsBytes);
       tma_load_2d(st, &amap, &X.full[t], X.c * 32, t * CB);
-      tma_load_2d(st + SS::kAStage, &csmap, &X.full[t], 0, t * CB - 1);
+      tma_load_2d(st + SP::kAStage, &csmap, &X.full[t], 0, t * CB - 1);
     }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5;
-  if constexpr (KR == 1) {
-    if (warp == 0) split_role<1, 0>(X);
-    else split_role<1, 1>(X);
-  } else {
-    if (warp == 0) split_role<2, 0>(X);
-    else if (warp == 1) split_role<2, 1>(X);
-    else if (warp == 2) split_role<2, 2>(X);
-    else split_role<2, 3>(X);
+  switch (warp) {
+    case 0: split_role<KR, 0>(X); break;
+    case 1: split_role<KR, 1>(X); break;
+    case 2: if constexpr (KR >= 2) split_role<KR, 2>(X); break;
+    case 3: if constexpr (KR >= 2) split_role<KR, 3>(X); break;
+    case 4: if constexpr (KR >= 3) split_role<KR, 4>(X); break;
+    case 5: if constexpr (KR >= 3) split_role<KR, 5>(X); break;
+    case 6: if constexpr (KR >= 4) split_role<KR, 6>(X); break;
+    default: if constexpr (KR >= 4) split_role<KR, 7>(X); break;
   }
 }
 

@@ -8,9 +8,11 @@ sequences left over (on the column stream or the wavefront kernel), signed
 zeros and infinities at the two ends of the column stream (where stages pass
 values through), and the full 8192 x 8192 matrix at k = 64 on sampled rows.
 FP64 cases: every group width (4, 8, 16, 32 lanes), k not a power of two
-(stages past k pass values through), ragged rows, padded leading dimensions,
-signed zeros and infinities, and 8192 x 8192 at k = 8 and 16 on sampled
-rows, bit-exact against the FP64 oracle."""
+(stages past k pass values through), the plans that leave up to 4
+sequences to the split column stream (at most one strip per SM, and more),
+ragged rows, padded leading dimensions, signed zeros and infinities, and
+8192 x 8192 at k = 8 and 16 on sampled rows, bit-exact against the FP64
+oracle."""
 import numpy as np
 import pytest
 
@@ -74,7 +76,7 @@ def test_pipe_f32_bit_exact(rs, m, n, k, slack):
 CASES64 = [  # m, n, k, lda slack: FP64, 3 <= k <= 32, n >= 256 (groups of 4, 8, 16 or 32 lanes)
     (8, 256, 3, 0), (9, 300, 4, 1), (33, 700, 5, 0), (100, 1024, 8, 3), (17, 257, 9, 0), (64, 1000, 16, 2),
     (5, 400, 17, 0), (71, 600, 31, 0), (40, 1100, 32, 1), (1, 256, 8, 0), (200, 333, 12, 0),
-    # k = 4j + 1 with m >= 64 and an even lda: passes, then the last sequence on the column stream
+    # k = 4j + 1 with m >= 64 and an even lda: passes, then the rest on the split column stream
     (64, 300, 5, 0), (100, 512, 13, 2), (128, 777, 21, 0), (96, 260, 29, 0),
     # the same k with an odd lda (no column stream): the last pass takes it
     (65, 300, 9, 0),
@@ -85,6 +87,20 @@ CASES64 = [  # m, n, k, lda slack: FP64, 3 <= k <= 32, n >= 256 (groups of 4, 8,
 # the resident warps allow (short ones for these few rows).
 CASES64 += [(64, 300, 33, 0), (70, 256, 34, 2), (40, 400, 40, 0), (100, 260, 61, 0), (33, 512, 64, 1),
             (9, 300, 33, 0)]
+
+# At most one 32-row strip per SM: full passes of 8, 16 and 32 for the
+# multiple of 8, the rest (up to 7) on the split column stream; up to 4096
+# rows, k >= 29 as one pass of 32 (k = 29, 31 here; 4200 rows: 16 + 8 + 6).
+CASES64 += [(100, 300, 10, 0), (64, 257, 11, 2), (70, 400, 12, 0), (96, 300, 18, 0), (128, 256, 20, 2),
+            (80, 512, 24, 0), (100, 300, 15, 0), (64, 400, 29, 0), (70, 256, 31, 2), (65, 260, 13, 1),
+            (64, 400, 21, 0), (70, 300, 23, 2), (4200, 256, 30, 0)]
+
+# More strips than SMs: passes of powers of two, remainders of 2 (past a
+# pass of 8) and of 3 (at most two strips per SM) on the split stream; k = 3
+# alone on it; with more than two strips per SM a remainder of 3 stays in a
+# pass of 4.
+CASES64 += [(4900, 256, 10, 0), (4900, 300, 11, 0), (5000, 256, 19, 0), (4900, 260, 26, 2), (5000, 256, 3, 0),
+            (9800, 256, 3, 0), (9800, 256, 11, 0)]
 
 
 @pytest.mark.parametrize("m,n,k,slack", CASES64)

@@ -1,6 +1,7 @@
-"""The column stream (one pass per 8 sequences) that rot_apply (k <= 16; the
-lane pipeline takes 3 <= k <= 32 when n >= 256) and rot_apply_f32 (k <= 41, or
-k <= 48 where the lane pipeline does not apply)
+"""The column stream (passes of up to 8 sequences; FP64 passes of up to 4 on
+the split stream) that rot_apply (k <= 16 where the lane pipeline does not
+apply, small k and the pipeline's remainders where it does) and
+rot_apply_f32 (k <= 41, or k <= 48 where the lane pipeline does not apply)
 take when A is TMA-addressable: bit-exact against the
 oracles on ragged shapes, padded leading dimensions, every k from 1 to 8 (so
 every window size and the k < window case), several passes (k = 9, 16, 23,
@@ -105,14 +106,18 @@ def test_stream_8192_k1_sampled_rows(rs):
     assert np.array_equal(bits(A32[idx].cpu().numpy()), bits(ref32))
 
 
-# FP64 passes of one or two sequences on column-major A run as two warps per
-# 32-row strip (one carrying the chain or the first sequence, the other the
-# finished columns or the second sequence), handing values over through a
-# ring of shared-memory tiles.  Ragged strips, padded leading dimensions, n
-# around the 20- and 21-column tiles and the ring's wrap (more than four
-# tiles), ±0 and infinities, bit-exact against the oracle.
+# FP64 passes of one to four sequences on column-major A run as two warps a
+# sequence per 32-row strip (one carrying the sequence's chain, the other
+# its finished columns, which feed the next sequence's pair), handing values
+# over through rings of shared-memory tiles.  Ragged strips, padded leading
+# dimensions, n around the 20-, 21- and 16-column tiles and the rings' wrap
+# (more than four tiles), k = 5..7 as a pass of four and the rest, ±0 and
+# infinities, bit-exact against the oracle.
 SPLIT_CASES = [(64, 64, 1, 0), (64, 64, 2, 0), (65, 81, 1, 2), (95, 80, 2, 4), (128, 126, 2, 0),
-               (200, 300, 1, 6), (333, 301, 2, 2), (1000, 1001, 2, 0), (97, 127, 1, 0), (160, 64, 2, 8)]
+               (200, 300, 1, 6), (333, 301, 2, 2), (1000, 1001, 2, 0), (97, 127, 1, 0), (160, 64, 2, 8),
+               (64, 64, 3, 0), (64, 64, 4, 0), (65, 81, 3, 2), (95, 200, 4, 4), (128, 126, 3, 0),
+               (333, 250, 4, 2), (97, 127, 3, 0), (160, 64, 4, 8), (1000, 255, 3, 0), (96, 100, 7, 0),
+               (200, 150, 6, 2), (130, 255, 5, 0), (64, 65, 4, 0), (64, 79, 3, 0)]
 
 
 @pytest.mark.parametrize("m,n,k,slack", SPLIT_CASES)
@@ -134,10 +139,12 @@ def test_stream_split_f64_bit_exact(rs, m, n, k, slack):
     assert np.all(np.isnan(out[m:, :n]))
 
 
-def test_stream_split_8192_k2_sampled_rows(rs):
-    m = n = 8192
+@pytest.mark.parametrize("m,n,k", [(8192, 8192, 2), (8192, 8192, 3), (4096, 4096, 4), (4096, 4096, 7)])
+def test_stream_split_full_size_sampled_rows(rs, m, n, k):
+    """Full-size matrices in the launch configuration of the library: two
+    strips per SM at k = 2 and 3, one at k = 4 and 7 (passes of 4 and 3)."""
     A = wl.matrix(m, n, 2)
-    C, S = wl.rotations(n, 2, 2)
+    C, S = wl.rotations(n, k, 2)
     r = np.random.default_rng(81)
     rows = np.unique(np.concatenate([[0, 31, 32, m - 1], r.choice(m, 28, replace=False)]))
     ref = oracle.rot_sequence(A[rows], C, S)
