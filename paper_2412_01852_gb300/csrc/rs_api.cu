@@ -58,12 +58,17 @@ rot_status rot_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda,
   bool quick;
   rot_status v = validate(m, n, k, A, lda, C, ldc, S, lds, &quick);
   if (v != ROT_OK || quick) return v;
-  // The column stream up to 41 sequences, the lane pipeline beyond (where
-  // each applies), the wavefront kernel otherwise.  With at most 4096 rows
-  // the stream has few warps (one per 32 rows) and the pipeline takes over
-  // from 20 sequences (measured: 4096 x 4096, k = 32: 0.48 ms against 0.77;
-  // 2048 x 2048, k = 24: about 0.33 against 0.39; at 8192 rows the two tie
-  // at k = 32..41, at 6144 the stream is 8 % faster).
+  // 16 to 55 sequences: the warp chain, eight warps per 32-row strip (k mod 8
+  // on the column stream after it; measured at 8192 x 8192: k = 32 0.81 ms
+  // against 1.36 for stream passes of 8, k = 48 1.03 against 1.82 for the
+  // lane pipeline).  Otherwise the column stream up to 41 sequences, the
+  // lane pipeline beyond (where each applies), the wavefront kernel
+  // otherwise.  With at most 4096 rows the stream has few warps (one per
+  // 32 rows) and the pipeline takes over from 20 sequences (measured: 4096 x
+  // 4096, k = 32: 0.48 ms against 0.77; 2048 x 2048, k = 24: about 0.33
+  // against 0.39).
+  if (rs::chain_f32_fits(m, n, k, A, lda))
+    return rs::chain_apply_f32(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream));
   const int64_t stream_max = m <= 4096 ? 19 : 41;
   if (k <= stream_max && rs::stream_fits<float>(m, n, k, A, lda))
     return rs::stream_apply<float>(m, n, k, A, lda, C, ldc, S, lds, static_cast<cudaStream_t>(stream));

@@ -53,6 +53,12 @@ template <typename T>
 rot_status stream_apply(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, const T* C, int64_t ldc,
                         const T* S, int64_t lds, cudaStream_t stream, bool packed = false);
 
+// FP32 warp chain (rs_chain.cu): whether it takes this problem (16 <= k <=
+// 55, A TMA-addressable as for the column stream), and the call.
+bool chain_f32_fits(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda);
+rot_status chain_apply_f32(int64_t m, int64_t n, int64_t k, float* A, int64_t lda, const float* C, int64_t ldc,
+                           const float* S, int64_t lds, cudaStream_t stream);
+
 // Rotations as a pipeline of sequences across a warp's lanes (rs_pipe.cu):
 // whether it takes this problem, and the call (FP32: k >= 32; FP64:
 // 3 <= k <= 32).
