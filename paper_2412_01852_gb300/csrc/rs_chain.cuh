@@ -62,51 +62,6 @@ struct ChainShape {
   static constexpr int kSmem = kBarOff + (2 * S + 2 * (NW - 1) * RING) * 8 + 16;
 };
 
-// Barrier waits of the chain, all bounded by kWaitLimitNs.  A barrier that
-// hands data over (a TMA stage filled, a ring slot written) is tested
-// first without suspending (most are complete when a warp gets there) and
-// waited on with acquire semantics; one that only reports a slot or stage
-// read (free, consumed) is arrived on and waited on relaxed: the reads it
-// reports have completed, since their values were used before the arrive.
-__device__ __forceinline__ bool mbar_test_acquire(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_try_relaxed(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.relaxed.cta.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void mbar_arrive_relaxed(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool chain_wait_data(uint64_t* bar, uint32_t parity) {
-  if (mbar_test_acquire(bar, parity)) return true;
-  return mbar_wait_bounded(bar, parity);
-}
-__device__ __forceinline__ bool chain_wait_read(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_relaxed(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer_ns();
-  for (;;) {
-    for (int r = 0; r < 64; ++r)
-      if (mbar_try_relaxed(bar, parity)) return true;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
-  }
-}
-
 // Shared state of one CTA of chain_kernel.
 struct ChainCta {
   const CUtensorMap* amap;
@@ -222,9 +177,9 @@ __device__ __forceinline__ void chain_role(const ChainCta& X, int w) {
     const int s = t % S, q = t % RING;
     const uint32_t use = (uint32_t)(t / RING);
     if (*X.abort_flag) break;
-    if (!settle(chain_wait_data(&X.full[s], (uint32_t)(t / S) & 1u))) break;
-    if (!FIRST && !settle(chain_wait_data(&X.ready[(w - 1) * RING + q], use & 1u))) break;
-    if (!LAST && t >= RING && !settle(chain_wait_read(&X.freed[w * RING + q], (use - 1) & 1u))) break;
+    if (!settle(mbar_wait_data(&X.full[s], (uint32_t)(t / S) & 1u))) break;
+    if (!FIRST && !settle(mbar_wait_data(&X.ready[(w - 1) * RING + q], use & 1u))) break;
+    if (!LAST && t >= RING && !settle(mbar_wait_read(&X.freed[w * RING + q], (use - 1) & 1u))) break;
     const float* in = FIRST ? reinterpret_cast<const float*>(X.smem + s * CS::kStage) + lane : ring(w - 1, q);
     const float2* cs = reinterpret_cast<const float2*>(X.smem + s * CS::kStage + CS::kAStage) + wk;
     float* out = LAST ? nullptr : ring(w, q);
@@ -250,7 +205,7 @@ __device__ __forceinline__ void chain_producer(const ChainCta& X) {
   int t = 0;
   for (; t + S < X.ntiles; ++t) {
     const int s = t % S;
-    bool ok = !*X.abort_flag && chain_wait_read(&X.consumed[s], (uint32_t)(t / S) & 1u);
+    bool ok = !*X.abort_flag && mbar_wait_read(&X.consumed[s], (uint32_t)(t / S) & 1u);
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) {
       if (X.lane == 0) {

@@ -104,6 +104,50 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+// Barrier waits of warps that hand tiles to one another (the warp chain,
+// the split column stream), all bounded by kWaitLimitNs.  A barrier that
+// hands data over (a TMA stage filled, a ring slot written) is tested
+// first without suspending (most are complete when a warp gets there) and
+// waited on with acquire semantics; one that only reports a slot or stage
+// read (free, consumed) is arrived on and waited on relaxed: the reads it
+// reports have completed, since their values were used before the arrive.
+__device__ __forceinline__ bool mbar_test_acquire(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_try_relaxed(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.relaxed.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive_relaxed(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_data(uint64_t* bar, uint32_t parity) {
+  if (mbar_test_acquire(bar, parity)) return true;
+  return mbar_wait_bounded(bar, parity);
+}
+__device__ __forceinline__ bool mbar_wait_read(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_relaxed(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (!mbar_try_relaxed(bar, parity))
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+
 // ---- TMA: 2-D tiled tensor load global -> shared, completes on an mbarrier ---
 __device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, uint64_t* bar,
                                             int x, int y) {

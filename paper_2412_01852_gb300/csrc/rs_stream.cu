@@ -74,7 +74,7 @@ rot_status stream_launch(int64_t m, int64_t n, int64_t k, T* A, int64_t lda, con
         auto kfn = stream_split_kernel<KR>;
         e = smem_opt_in(reinterpret_cast<const void*>(kfn), SplitShape<KR>::kSmem);
         if (e != cudaSuccess) { st = cuda_failed(e, "stream: shared-memory opt-in"); break; }
-        kfn<<<(unsigned)((m + 31) / 32), 64 * KR, SplitShape<KR>::kSmem, s>>>(amap, csmap, A, lda, (int)m, (int)n,
+        kfn<<<(unsigned)((m + 31) / 32), 64 * KR + 32, SplitShape<KR>::kSmem, s>>>(amap, csmap, A, lda, (int)m, (int)n,
                                                                               status);
         trace_end(tr, s);
         e = cudaGetLastError();

@@ -175,8 +175,13 @@ stream_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
 // Every element sees rotate_dmul's operations on the same operands, in the
 // same order: bit-identical.  Values pass between warps through rings of
 // RING tiles of CB values per lane in shared memory (ready/free barriers);
-// the TMA stages are read by every warp and refilled by the last one, once
-// the others are done with them.
+// the TMA stages are read by every warp and refilled by one more, producer
+// warp once all of them are done with a stage.  Only the barriers that hand
+// data over (a filled stage, a written ring slot) are waited on with
+// acquire semantics, after a test that does not suspend; the free and
+// consumed barriers, which only report reads, are arrived on and waited on
+// relaxed (the reads have completed: their values were used before the
+// arrive).
 // Each warp's role is a template parameter, so a chain warp's per-column path
 // holds nothing but its two FP64 instructions, their loads and the hand-off
 // store (with the roles as runtime branches: k = 1 1.33 ms).  Measured at
@@ -247,8 +252,9 @@ __device__ __forceinline__ void split_role(const SplitCta& X) {
   auto ring = [&](int g, int q) {
     return reinterpret_cast<double*>(X.smem + SP::kRingOff) + ((size_t)g * RING + q) * CB * 32 + lane;
   };
-  auto wait = [&](uint64_t* bar, uint32_t parity) {
-    bool ok = !*X.abort_flag && mbar_wait_bounded(bar, parity);
+  // Every lane's wait must succeed, else the warp leaves and the others
+  // learn it from the abort flag.
+  auto settle = [&](bool ok) {
     ok = __all_sync(0xffffffffu, ok);
     if (!ok && lane == 0) {
       if (!*X.abort_flag) set_error(X.status, kDevTimeoutTma);
@@ -256,26 +262,17 @@ __device__ __forceinline__ void split_role(const SplitCta& X) {
     }
     return ok;
   };
-  auto issue = [&](int t) {
-    const int s = t % S;
-    unsigned char* st = X.smem + s * SP::kStage;
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&X.full[s], SP::kABytes + SP::kCsBytes);
-    tma_load_2d(st, X.amap, &X.full[s], X.c * 32, t * CB);
-    tma_load_2d(st + SP::kAStage, X.csmap, &X.full[s], 0, t * CB - 1);
-  };
   const bool rowok = X.c * 32 + lane < X.m;
   double x = 0.0;                               // a chain's carried value
   double* ps = X.A + (int64_t)X.c * 32 + lane;  // the last warp's next column
-  int issued = X.ntiles < S ? X.ntiles : S;
-  int t = 0;
-  for (; t < X.ntiles; ++t) {
+  for (int t = 0; t < X.ntiles; ++t) {
     const int s = t % S, q = t % RING;
     const uint32_t use = (uint32_t)(t / RING);
-    if (!wait(&X.full[s], (uint32_t)(t / S) & 1u)) break;
-    if (kReadsPrev && !wait(&X.ready[(W - 1) * RING + q], use & 1u)) break;
-    if (kReadsIn && !wait(&X.ready[(W - 2) * RING + q], use & 1u)) break;
-    if (kWrites && t >= RING && !wait(&X.freed[W * RING + q], (use - 1) & 1u)) break;
+    if (*X.abort_flag) break;
+    if (!settle(mbar_wait_data(&X.full[s], (uint32_t)(t / S) & 1u))) break;
+    if (kReadsPrev && !settle(mbar_wait_data(&X.ready[(W - 1) * RING + q], use & 1u))) break;
+    if (kReadsIn && !settle(mbar_wait_data(&X.ready[(W - 2) * RING + q], use & 1u))) break;
+    if (kWrites && t >= RING && !settle(mbar_wait_read(&X.freed[W * RING + q], (use - 1) & 1u))) break;
     const double* at = reinterpret_cast<const double*>(X.smem + s * SP::kStage) + lane;
     const V2* cs = reinterpret_cast<const V2*>(X.smem + s * SP::kStage + SP::kAStage) + kSeq;
     double* out = kWrites ? ring(W, q) : nullptr;
@@ -313,30 +310,48 @@ __device__ __forceinline__ void split_role(const SplitCta& X) {
         }
       }
     }
-    if constexpr (kWrites) mbar_arrive(&X.ready[W * RING + q]);
-    if constexpr (kReadsPrev) mbar_arrive(&X.freed[(W - 1) * RING + q]);
-    if constexpr (kReadsIn) mbar_arrive(&X.freed[(W - 2) * RING + q]);
-    if constexpr (!kLast) {
-      mbar_arrive(&X.consumed[s]);
-    } else {
-      // The last reader of stage s: refill it with tile t + S once the
-      // other warps are done with it.
-      __syncwarp();
-      if (t + S < X.ntiles) {
-        if (!wait(&X.consumed[s], (uint32_t)(t / S) & 1u)) break;
-        if (lane == 0) issue(t + S);
-        ++issued;
-      }
-    }
+    if constexpr (kWrites) mbar_arrive(&X.ready[W * RING + q]);   // release: the slot's values
+    if constexpr (kReadsPrev) mbar_arrive_relaxed(&X.freed[(W - 1) * RING + q]);
+    if constexpr (kReadsIn) mbar_arrive_relaxed(&X.freed[(W - 2) * RING + q]);
+    mbar_arrive_relaxed(&X.consumed[s]);
   }
-  // On a timeout, let the copies still in flight (from tile t on) land before
-  // leaving; one that already landed returns at once.
-  if (kLast && t < X.ntiles && lane == 0)
+}
+
+// The producer warp: refills stage s with tile t + S once every compute
+// warp is done with tile t; the CTA ends only once its last copies (all of
+// them after a timeout) have landed.
+template <int KR>
+__device__ __forceinline__ void split_producer(const SplitCta& X) {
+  using SP = SplitShape<KR>;
+  constexpr int CB = SP::CB, S = SP::S;
+  int issued = X.ntiles < S ? X.ntiles : S;
+  int t = 0;
+  for (; t + S < X.ntiles; ++t) {
+    const int s = t % S;
+    bool ok = !*X.abort_flag && mbar_wait_read(&X.consumed[s], (uint32_t)(t / S) & 1u);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) {
+      if (X.lane == 0) {
+        if (!*X.abort_flag) set_error(X.status, kDevTimeoutTma);
+        *X.abort_flag = 1;
+      }
+      break;
+    }
+    if (X.lane == 0) {
+      unsigned char* st = X.smem + s * SP::kStage;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&X.full[s], SP::kABytes + SP::kCsBytes);
+      tma_load_2d(st, X.amap, &X.full[s], X.c * 32, (t + S) * CB);
+      tma_load_2d(st + SP::kAStage, X.csmap, &X.full[s], 0, (t + S) * CB - 1);
+    }
+    ++issued;
+  }
+  if (X.lane == 0)
     for (int u = t; u < issued; ++u) (void)mbar_wait_bounded(&X.full[u % S], (uint32_t)(u / S) & 1u);
 }
 
 template <int KR>
-__global__ void __launch_bounds__(64 * KR)
+__global__ void __launch_bounds__(64 * KR + 32)
 stream_split_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap csmap, double* A,
                     int64_t lda, int m, int n, int* status) {
   static_assert(KR >= 1 && KR <= 4, "one to four sequences");
@@ -365,7 +380,7 @@ stream_split_kernel(const __grid_constant__ CUtensorMap amap, const __grid_const
     prefetch_tmap(&csmap);
     for (int s = 0; s < S; ++s) {
       mbar_init(&X.full[s], 1);
-      mbar_init(&X.consumed[s], 32 * (NW - 1));   // every warp but the last
+      mbar_init(&X.consumed[s], 32 * NW);       // every compute warp
     }
     for (int g = 0; g < NRING; ++g)
       for (int q = 0; q < RING; ++q) {
@@ -394,8 +409,10 @@ stream_split_kernel(const __grid_constant__ CUtensorMap amap, const __grid_const
     case 4: if constexpr (KR >= 3) split_role<KR, 4>(X); break;
     case 5: if constexpr (KR >= 3) split_role<KR, 5>(X); break;
     case 6: if constexpr (KR >= 4) split_role<KR, 6>(X); break;
-    default: if constexpr (KR >= 4) split_role<KR, 7>(X); break;
+    case 7: if constexpr (KR >= 4) split_role<KR, 7>(X); break;
+    default: break;
   }
+  if (warp == NW) split_producer<KR>(X);
 }
 
 }  // namespace rs
