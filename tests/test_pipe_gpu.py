@@ -1,6 +1,7 @@
 """The lane pipeline (rs_pipe.cu).  FP32: rot_apply_f32 takes it for n >= 1024
-and k >= 42, or k >= 20 with at most 4096 rows (and for k >= 20 where the
-column stream does not apply);
+and k >= 56, and from k = 42 (k = 20 with at most 4096 rows) where the warp
+chain does not apply (fewer than 64 rows, a leading dimension TMA cannot
+address, or k = 8j + 7 with at most 4096 rows);
 FP64: rot_apply (and rot_apply_left) for 3 <= k <= 32 and n >= 256.  FP32 cases: bit-exact against
 the FP32 oracle on ragged row counts, padded leading dimensions, every pass
 width (32 .. 192 sequences), several passes (k = 224, 384, 448), the k mod 32
@@ -57,6 +58,9 @@ CASES = [  # m, n, k, lda slack
     (70, 1024, 223, 0),
     # 20 <= k < 32 with few rows: a single part-filled pass
     (64, 1024, 20, 0), (100, 1100, 31, 3), (9, 1024, 24, 0),
+    # k = 8j + 7 with at most 4096 rows and an aligned A: the warp chain
+    # leaves these to the pipeline
+    (64, 1024, 31, 0), (100, 1024, 47, 0),
 ]
 
 
