@@ -211,9 +211,11 @@ rot_status rot_unpack_f32(int64_t m, int64_t n, const float* P, float* A, int64_
  * for bit (rows are independent and each row sees the same operations).
  * Few sequences (k <= 16 in FP64, k <= 48 in FP32, with m, n >= 64 and P
  * 16-byte aligned) run the column stream over the strips; otherwise the
- * wavefront kernel.  The lane pipelines that rot_apply uses for
- * 3 <= k <= 32 (FP64) and k > 48 (FP32) are not used here, so those k run
- * slower than on a column-major matrix.  Same error codes as rot_apply.
+ * wavefront kernel.  What rot_apply uses on a column-major matrix beyond
+ * that (the FP64 column stream split over warps, the lane pipelines for
+ * 3 <= k <= 32 in FP64 and k > 55 in FP32, and the FP32 warp chain for
+ * 16 <= k <= 55) is not used here, so those k run slower than on a
+ * column-major matrix.  Same error codes as rot_apply.
  */
 rot_status rot_apply_packed(int64_t m, int64_t n, int64_t k, double* P, const double* C, int64_t ldc,
                             const double* S, int64_t lds, void* stream);
